@@ -1,0 +1,290 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the dsDNA engine (arXiv:1608.03722 model) on GB300.
+
+Workload (default): 1 Mbp dsDNA, 2e6 nucleotides, confined self-avoiding helix
+in a periodic cube at volume fraction 0.05, Langevin at kT = 1, FP32 forces
+with FP64 accumulation.  One bench step = ``--md-steps`` (default 100)
+Langevin timesteps of the whole system (forces of App. A, Langevin update,
+neighbour-list rebuilds as needed), queued through the C ABI.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (one Langevin step of the same workload per bench step).
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "nucleotide-timesteps/s at 1 Mbp (fraction of HBM roofline); batched/surrogate vs plain"
+UNIT = "nucleotide-timesteps/s"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_workload(name: str, seed: int = 0):
+    from paper_1608_03722_gb300 import inputs as I
+    if name == "c3":
+        cfg = I.c3_confined(seed=seed)
+        desc = ("confined self-avoiding dsDNA, 1,000,000 bp = 2,000,000 nucleotides, periodic cube "
+                f"L={cfg.box[0]:.2f} nm (volume fraction 0.05), Langevin kT=1, dt=0.005")
+    elif name == "c2":
+        cfg = I.c2_tethered(force=5.0, torque=2.0, seed=seed)
+        desc = "tethered linear dsDNA, 10 kbp = 20,000 nucleotides, f=5 kT/nm, torque 2 kT"
+    elif name == "c4":
+        cfg = I.c4_batch(seed=seed)
+        desc = f"256 independent molecules, lengths log-uniform 500-20000 bp ({cfg.n_nt} nucleotides)"
+    elif name == "c1":
+        cfg = I.c1_linear(200, seed=seed)
+        desc = "linear dsDNA, 200 bp = 400 nucleotides, open boundaries"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return cfg, desc
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def run_cpu_oracle(cfg, steps: int, seconds_cap: float = 25.0):
+    """Time the FP64 oracle (as it stands, cell-hash pair search) on whole Langevin steps of the workload."""
+    import oracle as O
+    p = O.params(box=cfg.box) if cfg.box[0] > 0 else O.params()
+    X, V, u, Om = (a.copy() for a in (cfg.X, cfg.V, cfg.u, cfg.Om))
+    done = 0
+    t0 = time.perf_counter()
+    while done < steps:
+        O.run(p, cfg.n_bp, X, V, u, Om, 1, step0=done, ext_f=cfg.ext_f, ext_t=cfg.ext_t, tether=cfg.tether,
+              cells=True)
+        done += 1
+        if time.perf_counter() - t0 > seconds_cap:
+            break
+    dt = time.perf_counter() - t0
+    return cfg.n_nt * done / dt, done, dt
+
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return 0
+    cfg, desc = build_workload(args.workload)
+    import oracle as O
+    O.build()
+    value, done, dt = run_cpu_oracle(cfg, args.steps, seconds_cap=max(30.0, 20.0 * args.steps))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": done,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(done, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "md_steps_per_step": 1, "l2": "state larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{done} whole Langevin steps of the full workload ({cfg.n_nt} nucleotides)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--md-steps", type=int, default=100)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, ws, rank)
+
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1608_03722_gb300 import dsdna as D
+
+    cfg, desc = build_workload(args.workload, seed=rank)
+    prec = D.PREC_MIXED if args.precision == "mixed" else D.PREC_FP64
+    p = D.dsdna_default_params(precision=prec, box=cfg.box, seed=rank)
+    ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether)
+    if cfg.ext_f is not None:
+        for m in range(len(cfg.n_bp)):
+            ctx.set_external_force_torque(m, cfg.ext_f[m], cfg.ext_t[m])
+    K, W, S = args.steps, args.warmup, args.md_steps
+    for _ in range(W):
+        ctx.step(S)
+    ctx.synchronize()
+    info0 = ctx.info()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(gpu_uuid(torch, local)) if rank == 0 else None
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        ctx.step(S)
+    e1.record()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ctx.synchronize()
+    ms = e0.elapsed_time(e1)
+    info1 = ctx.info()
+    t_local = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    nt_steps = cfg.n_nt * S * K * ws
+    value = nt_steps / (ms_max * 1e-3)
+
+    # neighbours per bead (full list), for the algorithmic byte count
+    nbar = 2.0 * len(ctx.neighbor_pairs()) / cfg.n_nt
+    graph_chunk = ctx.info()["steps_per_graph"] if "steps_per_graph" in ctx.info() else 50
+    launches_per_step = (S + graph_chunk - 1) // graph_chunk
+    rebuilds = info1["rebuilds"] - info0["rebuilds"]
+
+    # algorithmic bytes per nucleotide-step of the fused force + Langevin kernel:
+    # state X,V (FP64) + u, Omega (FP32) read and written, position mirror read and written,
+    # topology word, neighbour count and list entries
+    state = 48 + 24 if prec == D.PREC_MIXED else 96
+    mirror = 32 if prec == D.PREC_MIXED else 48
+    b_nt = 2 * state + 2 * mirror + 4 + 4 + 4 * nbar
+    per_launch_bytes = b_nt * cfg.n_nt * graph_chunk
+    launch_s = ms_max * 1e-3 / (K * launches_per_step)
+    hbm, peak_kind = peaks()
+    achieved = per_launch_bytes / launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "peak_kind": peak_kind, "bytes_per_nt_step": b_nt, "neighbors_per_bead": nbar,
+            "kernel": "engine_kernel<float,STEP> (fused forces + Langevin, persistent cooperative)"}
+
+    # end to end through the C ABI with host buffers: upload state, step, download state
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        X, V, u, Om = ctx.get_state()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(K, 3))
+        for _ in range(n_e2e):
+            ctx.set_state(-1, X, V, u, Om)
+            ctx.step(S)
+            X, V, u, Om = ctx.get_state()
+        dt_e2e = time.perf_counter() - t0
+        e2e = {"value": cfg.n_nt * S * n_e2e / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * 3 * 8 * cfg.n_nt,
+               "d2h_bytes_per_step": 4 * 3 * 8 * cfg.n_nt, "steps": n_e2e}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, done, dt = run_cpu_oracle(cfg, 3, seconds_cap=25.0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} whole Langevin step(s) of the full workload ({cfg.n_nt} nucleotides), "
+                         f"{dt:.1f} s, single thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == D.PREC_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": desc, "md_steps_per_step": S, "n_nucleotides": cfg.n_nt,
+                       "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (state > 129 MB)",
+                       "rebuilds_in_timed_region": rebuilds, "graph_steps_per_launch": graph_chunk},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": K * launches_per_step, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

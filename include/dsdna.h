@@ -1,0 +1,228 @@
+/*
+ * dsdna.h -- C ABI of the GB300 (sm_103a) engine for the single-nucleotide
+ * double-stranded DNA model of Fosado, Michieletto, Allan, Brackley, Henrich
+ * and Marenduzzo, "A single nucleotide resolution model for large-scale
+ * simulations of double stranded DNA" (arXiv:1608.03722).
+ *
+ * What the engine computes (paper references are to that article):
+ *   - Each nucleotide is a rigid body: a backbone bead with excluded volume
+ *     and a base patch a distance ell = 0.5 from it (Sec. 2, Fig. 1a).
+ *   - Interactions (App. A, Eqs. 9-15, Table 1): FENE + WCA backbone bond
+ *     between consecutive beads of a strand, breakable harmonic hydrogen bond
+ *     between paired patches, typed WCA excluded volume between beads (steric
+ *     beads every third nucleotide, ghosts interacting only with the other
+ *     strand at sigma = 0.5, Sec. 2 / Fig. 1d), dihedral A-E-F-B, Morse
+ *     stacking between consecutive patches, planarity angle E-F-B and
+ *     Kratky-Porod bending of three consecutive patches.
+ *   - Langevin dynamics (App. A Eq. 8) with the velocity-Verlet step of
+ *     App. A Eq. 16, applied per site and summed over the rigid body.
+ *   - Loads of the single-molecule experiments (Sec. 4.1, 4.2): base pair 0
+ *     anchored, a force and a torque on the last base pair.
+ *   - Observables: extension R_z (Sec. 4.1), twist from base-pair frames
+ *     (Sec. 3.2, App. B), linking number by the Gauss integral of the closed
+ *     strands (App. C Eq. 17), denatured fraction (Sec. 5).
+ *
+ * Layout of host arrays: AoS, X[3*g + c], with nucleotide slot
+ * g = 2*(bp_offset(mol) + k) + s; s = 0 is strand A nucleotide k, s = 1 its
+ * partner on strand B.  Strand A runs 5'->3' with increasing k, strand B with
+ * decreasing k.  X is the centre of mass of the nucleotide (midpoint of bead
+ * and patch), u the unit vector from bead to patch; V and Om are the
+ * half-step (leapfrog) centre and angular velocities, Om normal to u.
+ * Positions must be unwrapped along each strand (no jump of a box length
+ * between consecutive nucleotides), also in a periodic box.
+ *
+ * Units are the paper's simulation units (Table 2): sigma = 1 nm,
+ * epsilon = kT, tau_Br.
+ *
+ * Ownership: the context owns every device buffer it allocates through the
+ * caller's allocator (or cudaMalloc when none is given) and frees them in
+ * dsdna_destroy.  Host arrays passed in or out belong to the caller and are
+ * only accessed during the call.  A context is bound to the CUDA device that
+ * was current at dsdna_create and to one stream; it is not thread-safe.
+ *
+ * Errors: every call returns DSDNA_OK (0) or a negative dsdna_status.  Work
+ * on the device is asynchronous: a device-side error (broken FENE bond,
+ * non-finite force, list overflow, barrier timeout) is reported by the next
+ * call that synchronises (dsdna_synchronize, get_state, energy_virial,
+ * observables, compute_forces).  After any error the context is poisoned:
+ * every call except set_state, last_error and destroy returns DSDNA_ESTATE
+ * until dsdna_set_state installs a new state.  The device never traps.
+ */
+#ifndef DSDNA_H
+#define DSDNA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSDNA_NTERMS 10
+/* energy[] slots of dsdna_energy_virial */
+enum {
+  DSDNA_E_FENE = 0,  /* App. A Eq. 9 */
+  DSDNA_E_BONDWCA,   /* Table 1 backbone WCA (sigma = 0.443) */
+  DSDNA_E_HBOND,     /* App. A Eq. 10 */
+  DSDNA_E_WCA,       /* App. A Eq. 11, typed per Sec. 2 */
+  DSDNA_E_DIHEDRAL,  /* App. A Eq. 12 */
+  DSDNA_E_MORSE,     /* App. A Eq. 13 */
+  DSDNA_E_PLANAR,    /* App. A Eq. 14 */
+  DSDNA_E_BEND,      /* App. A Eq. 15 */
+  DSDNA_E_KIN_T,     /* translational kinetic energy, full-step velocity */
+  DSDNA_E_KIN_R      /* rotational kinetic energy, full-step velocity */
+};
+
+typedef enum dsdna_status {
+  DSDNA_OK = 0,
+  DSDNA_EINVAL = -1,    /* bad argument */
+  DSDNA_ENOMEM = -2,    /* allocation failed */
+  DSDNA_ECUDA = -3,     /* CUDA runtime error */
+  DSDNA_EFENE = -4,     /* a backbone bond reached R0 (App. A Eq. 9: U = infinity) */
+  DSDNA_ENAN = -5,      /* non-finite force or velocity */
+  DSDNA_EOVERFLOW = -6, /* neighbour list capacity or image range exceeded */
+  DSDNA_ETIMEOUT = -7,  /* bounded device barrier gave up */
+  DSDNA_ESTATE = -8     /* context poisoned by an earlier error */
+} dsdna_status;
+
+enum { DSDNA_PREC_MIXED = 0, DSDNA_PREC_FP64 = 1 };
+enum { DSDNA_NOISE_OFF = 0, DSDNA_NOISE_UNIFORM = 1, DSDNA_NOISE_GAUSSIAN = 2 };
+
+/* Model, integrator and engine parameters.  dsdna_default_params fills the
+ * values of Table 1 (force field), Sec. 2 (geometry), App. A (kT = 1,
+ * gamma = 1, dt = 0.005 tau_Br, Eq. 16). */
+typedef struct dsdna_params {
+  double K1, R0, eps_bb, sigma_bb;       /* FENE + backbone WCA */
+  double K2, r0_hb, rc_hb;               /* hydrogen bond */
+  double eps_ev, sigma_ss, sigma_cross;  /* steric WCA: steric pair of one strand / any pair across strands */
+  double K3, d_dih;                      /* dihedral, d in radians (-144 deg) */
+  double K4, lambda_m, r0_m;             /* Morse stacking */
+  double K5, alpha0;                     /* planarity (K5/2)(alpha - alpha0)^2, alpha0 in radians */
+  double K6;                             /* Kratky-Porod bending */
+  double mass;                           /* mass of each site (bead and patch) */
+  double ell;                            /* bead-patch distance */
+  double kT, gamma, dt;                  /* Langevin temperature, friction per site, time step */
+  uint64_t seed;                         /* Philox key */
+  int noise;                             /* DSDNA_NOISE_* */
+  int steric_phase;                      /* steric iff (index along strand from its 5' end) % 3 == phase */
+  double box[3];                         /* > 0: periodic edge in that direction; <= 0: open */
+  double skin;                           /* neighbour-list skin (0: default 0.3) */
+  int precision;                         /* DSDNA_PREC_MIXED (FP32 forces, FP64 X/V) or DSDNA_PREC_FP64 */
+  int max_neighbors;                     /* neighbour capacity per bead (0: default 32) */
+  int block_threads;                     /* nucleotides per CTA segment (0: default 256; 64..512, multiple of 32) */
+  int blocks_per_sm;                     /* persistent CTAs per SM (0: as many as fit) */
+  int steps_per_graph;                   /* steps per captured CUDA graph launch (0: default 50) */
+} dsdna_params;
+
+/* Molecules and (optional) initial state.  NULL X/u builds ideal relaxed
+ * helices along +z from the origin (Sec. 2); NULL V/Om draws Maxwell-Boltzmann
+ * velocities from the Philox stream of the seed.  tether[m] != 0 anchors base
+ * pair 0 of molecule m (Sec. 4.1).  Molecules never interact with each other. */
+typedef struct dsdna_system {
+  int n_mol;
+  const int* n_bp;       /* [n_mol], each >= 1 */
+  const double* X;       /* [3*n_nt] or NULL */
+  const double* V;       /* [3*n_nt] or NULL */
+  const double* u;       /* [3*n_nt] or NULL (with X) */
+  const double* Om;      /* [3*n_nt] or NULL (with V) */
+  const int* tether;     /* [n_mol] or NULL */
+} dsdna_system;
+
+/* Device allocator used for every buffer of a context.  NULL: cudaMalloc/cudaFree. */
+typedef struct dsdna_allocator {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*release)(void* ptr, void* user);
+  void* user;
+} dsdna_allocator;
+
+typedef struct dsdna_obs {
+  double rz;        /* extension along z of the base-pair centres (Sec. 4.1) */
+  double denat;     /* fraction of base pairs with broken hydrogen bond (Sec. 5) */
+  double tw;        /* twist in turns, sum of (alpha + gamma) / 2 pi (Sec. 3.2, App. B) */
+  double tw_ideal;  /* twist of the relaxed helix of the same length: (N-2) steps x 36 deg */
+  double lk;        /* linking number of the closed strands (App. C Eq. 17) */
+  double wr;        /* writhe lk - tw (Sec. 4.2, Eq. 6) */
+} dsdna_obs;
+
+enum { DSDNA_OBS_EXT = 1, DSDNA_OBS_DENAT = 2, DSDNA_OBS_TW = 4, DSDNA_OBS_LK = 8 };
+
+typedef struct dsdna_info {
+  int64_t n_nt;          /* nucleotides */
+  int n_mol;
+  int64_t step;          /* step counter */
+  int64_t rebuilds;      /* neighbour-list builds so far */
+  int grid_blocks;       /* persistent CTAs */
+  int block_threads;
+  int max_neighbors;
+  int precision;
+  double skin;
+  int64_t cell_table;    /* entries of the cell hash table */
+  int64_t device_bytes;  /* bytes allocated on the device */
+} dsdna_info;
+
+typedef struct dsdna_ctx dsdna_ctx;
+
+/* Fill p with the defaults described above. */
+void dsdna_default_params(dsdna_params* p);
+
+/* Create a context.  params, sys: read during the call.  alloc: may be NULL.
+ * cuda_stream: cudaStream_t all work is queued on (NULL = legacy default).
+ * Returns DSDNA_EINVAL for inconsistent input, DSDNA_ENOMEM, DSDNA_ECUDA. */
+int dsdna_create(const dsdna_params* params, const dsdna_system* sys, const dsdna_allocator* alloc,
+                 void* cuda_stream, dsdna_ctx** out);
+
+/* Set the applied end force f (force on the last base pair, split over its
+ * two nucleotides) and torque t (couple on the same pair) of molecule mol;
+ * mol = -1 sets every molecule (Sec. 4.1 Fig. 5, Sec. 4.2 Fig. 7). */
+int dsdna_set_external_force_torque(dsdna_ctx* ctx, int mol, const double force[3], const double torque[3]);
+
+/* Queue nsteps Langevin steps (App. A Eq. 8, Eq. 16) on the context's stream;
+ * returns without waiting.  Neighbour lists are rebuilt on the device when a
+ * bead moved more than skin/2 since the last build. */
+int dsdna_step(dsdna_ctx* ctx, int64_t nsteps);
+
+/* Wait for queued work; returns the first device-side error, if any. */
+int dsdna_synchronize(dsdna_ctx* ctx);
+
+/* Energy per term (DSDNA_E_*) and site virial W = sum (r_s - r_ref) (x) F_s
+ * (xx yy zz xy xz yz) of molecule mol (-1: sum over all), FP64 reductions.
+ * Kinetic terms use the full-step velocities of the current step. */
+int dsdna_energy_virial(dsdna_ctx* ctx, int mol, double energy[DSDNA_NTERMS], double virial[6]);
+
+/* Observables of molecule mol selected by flags (DSDNA_OBS_*), FP64
+ * reductions on the device.  DSDNA_OBS_LK costs O(N^2) in the molecule length. */
+int dsdna_observables(dsdna_ctx* ctx, int mol, unsigned flags, dsdna_obs* out);
+
+/* Copy the state of molecule mol (-1: all) to caller-owned host arrays
+ * [3*n] each (any may be NULL).  Synchronises. */
+int dsdna_get_state(dsdna_ctx* ctx, int mol, double* X, double* V, double* u, double* Om);
+
+/* Install a new state for molecule mol (-1: all) from host arrays (NULL
+ * leaves that field unchanged); clears a poisoned context and forces a
+ * neighbour-list rebuild. */
+int dsdna_set_state(dsdna_ctx* ctx, int mol, const double* X, const double* V, const double* u, const double* Om);
+
+/* Conservative site forces (bead, patch) on every nucleotide at the current
+ * state, including the applied loads, as FP64 host arrays [3*n_nt] each. */
+int dsdna_compute_forces(dsdna_ctx* ctx, double* F_bead, double* F_patch);
+
+/* Build the neighbour list at the current state and return its pairs
+ * (i < j, global slots) within r_cut(type) + skin: writes min(count, cap)
+ * pairs to pi/pj and the total to *count. */
+int dsdna_neighbor_pairs(dsdna_ctx* ctx, int64_t cap, int64_t* pi, int64_t* pj, int64_t* count);
+
+int dsdna_get_info(const dsdna_ctx* ctx, dsdna_info* info);
+
+/* Step counter (number of steps queued so far). */
+int64_t dsdna_step_counter(const dsdna_ctx* ctx);
+
+/* Text of the last error of ctx (or of the last failed create when ctx is NULL). */
+const char* dsdna_last_error(const dsdna_ctx* ctx);
+
+/* Release every device buffer and the context. */
+void dsdna_destroy(dsdna_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSDNA_H */

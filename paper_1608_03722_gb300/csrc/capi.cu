@@ -1,0 +1,769 @@
+// capi.cu -- host engine behind the C ABI of include/dsdna.h.
+//
+// Owns the device buffers of a context, builds the topology flags of the
+// dsDNA model (Sec. 2: strands, partners, steric / ghost beads, anchored and
+// loaded base pairs of Sec. 4), converts states between the caller's AoS
+// host arrays and the engine's SoA device layout, and queues the persistent
+// engine kernel (engine_kernels.cuh) as captured CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dsdna.h"
+#include "engine.cuh"
+#include "obs.h"
+
+namespace dsdna {
+template <class Real> cudaError_t engine_occupancy(int mode, int T, int* blocks_per_sm, size_t* smem);
+template <class Real> cudaError_t engine_launch(int mode, const KArgs<Real>& a, int grid, int T, size_t smem, cudaStream_t st);
+}  // namespace dsdna
+
+using namespace dsdna;
+
+static thread_local std::string g_create_error;
+
+struct dsdna_ctx {
+  dsdna_params p{};
+  int device = 0;
+  cudaStream_t st = nullptr;
+  dsdna_allocator alloc{};
+  bool have_alloc = false;
+  int n_mol = 0;
+  std::vector<int> n_bp;
+  std::vector<int64_t> off;      // bp offsets [n_mol + 1]
+  std::vector<int> tether;
+  std::vector<double> ext;       // [n_mol][8]
+  int64_t n = 0;
+  int maxN = 0;
+  std::vector<void*> bufs;
+  int64_t bytes = 0;
+  // device buffers
+  double* X = nullptr; double* V = nullptr; void* Om = nullptr;
+  int4* Kw = nullptr; float4* U = nullptr; double* ud = nullptr;
+  int* topo = nullptr; int* img = nullptr; int* kref = nullptr; int* nbr = nullptr; int* ncnt = nullptr;
+  unsigned* cnt = nullptr; unsigned* start = nullptr; int* key = nullptr;
+  float4* cent = nullptr; float4* wpos = nullptr; unsigned* bsum = nullptr;
+  int64_t* mol_off = nullptr; double* ext_d = nullptr;
+  GridBar* bar = nullptr; unsigned* err = nullptr; int64_t* step_d = nullptr; int* rebuild = nullptr;
+  unsigned long long* nrebuild = nullptr;
+  double* fout = nullptr; double* eout = nullptr; double* stage = nullptr;
+  double* obs_scratch = nullptr; double* obs_out = nullptr;
+  unsigned H = 0;
+  int morton_bits = 0;
+  int nc[3] = {0, 0, 0};
+  double cellh = 0;
+  // launch
+  int T = 256;
+  int64_t nseg = 0;
+  int grid[3] = {0, 0, 0};
+  size_t smem[3] = {0, 0, 0};
+  cudaGraphExec_t gexec = nullptr;
+  int64_t gsteps = 0;
+  bool graph_failed = false;
+  int64_t step = 0;
+  bool poisoned = false;
+  std::string errmsg;
+  KArgs<float> kf{};
+  KArgs<double> kd{};
+  bool fp64() const { return p.precision == DSDNA_PREC_FP64; }
+};
+
+// ---------------------------------------------------------------- helpers
+static int fail(dsdna_ctx* c, int code, const std::string& msg) {
+  if (c) c->errmsg = msg; else g_create_error = msg;
+  return code;
+}
+static int cuda_fail(dsdna_ctx* c, cudaError_t e, const char* what) {
+  if (c) c->poisoned = true;
+  return fail(c, DSDNA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+static void* dalloc(dsdna_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (c->have_alloc) {
+    p = c->alloc.alloc(bytes, c->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) { c->bufs.push_back(p); c->bytes += (int64_t)bytes; }
+  return p;
+}
+
+static void free_all(dsdna_ctx* c) {
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  for (void* p : c->bufs) {
+    if (c->have_alloc) c->alloc.release(p, c->alloc.user);
+    else cudaFree(p);
+  }
+  c->bufs.clear();
+}
+
+// Philox4x32-10 (Salmon et al., SC'11) for the host-side initial velocities.
+static void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t m0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t m1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t x0 = (uint32_t)(m1 >> 32) ^ c[1] ^ k0;
+    const uint32_t x2 = (uint32_t)(m0 >> 32) ^ c[3] ^ k1;
+    c[1] = (uint32_t)m1;
+    c[3] = (uint32_t)m0;
+    c[0] = x0;
+    c[2] = x2;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Relaxed helix of Sec. 2: patches of base pair k on the z axis at rise*k,
+// beads ell off the axis at azimuth k*(d+180 deg), partner on the opposite side.
+static void host_helix(const dsdna_params& p, int N, double* X, double* u) {
+  const double tw = p.d_dih + M_PI;
+  for (int k = 0; k < N; ++k)
+    for (int s = 0; s < 2; ++s) {
+      const double a = tw * k + (s ? M_PI : 0.0);
+      const double cx = std::cos(a), cy = std::sin(a);
+      const int64_t g = 2 * (int64_t)k + s;
+      X[3 * g + 0] = 0.5 * p.ell * cx;
+      X[3 * g + 1] = 0.5 * p.ell * cy;
+      X[3 * g + 2] = p.r0_m * k;
+      u[3 * g + 0] = -cx;
+      u[3 * g + 1] = -cy;
+      u[3 * g + 2] = 0.0;
+    }
+}
+
+// Maxwell-Boltzmann draw: Box-Muller normals of the Philox stream with
+// counter (local nucleotide, 2^32-1, 2^32-1, 2*mol + block), angular
+// velocity normal to u, net momentum of the mobile nucleotides removed.
+static void host_maxwell(const dsdna_params& p, int mol, int N, const double* u, int tether, double* V, double* Om) {
+  const double M = 2.0 * p.mass, I = 0.5 * p.mass * p.ell * p.ell;
+  const int64_t n = 2 * (int64_t)N;
+  const double sv = std::sqrt(p.kT / M), sw = std::sqrt(p.kT / I);
+  for (int64_t l = 0; l < n; ++l) {
+    double z[8];
+    for (int b = 0; b < 2; ++b) {
+      uint32_t c[4] = {(uint32_t)l, 0xFFFFFFFFu, 0xFFFFFFFFu, (uint32_t)(2 * mol + b)};
+      philox_host(c, (uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+      for (int q = 0; q < 2; ++q) {
+        const double ua = ((double)c[2 * q] + 0.5) / 4294967296.0;
+        const double ub = ((double)c[2 * q + 1] + 0.5) / 4294967296.0;
+        const double rad = std::sqrt(-2.0 * std::log(ua));
+        z[4 * b + 2 * q] = rad * std::cos(2.0 * M_PI * ub);
+        z[4 * b + 2 * q + 1] = rad * std::sin(2.0 * M_PI * ub);
+      }
+    }
+    const double* ul = u + 3 * l;
+    double ax[3] = {0, 0, 1};
+    if (std::fabs(ul[2]) > 0.9) { ax[0] = 1; ax[2] = 0; }
+    double e1[3] = {ul[1] * ax[2] - ul[2] * ax[1], ul[2] * ax[0] - ul[0] * ax[2], ul[0] * ax[1] - ul[1] * ax[0]};
+    const double le = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (double& x : e1) x /= le;
+    const double e2[3] = {ul[1] * e1[2] - ul[2] * e1[1], ul[2] * e1[0] - ul[0] * e1[2], ul[0] * e1[1] - ul[1] * e1[0]};
+    for (int q = 0; q < 3; ++q) {
+      V[3 * l + q] = sv * z[q];
+      Om[3 * l + q] = sw * (z[3] * e1[q] + z[4] * e2[q]);
+    }
+  }
+  const int64_t first = tether ? 2 : 0;
+  double mean[3] = {0, 0, 0};
+  for (int64_t l = first; l < n; ++l) for (int q = 0; q < 3; ++q) mean[q] += V[3 * l + q];
+  if (n > first) for (double& m : mean) m /= (double)(n - first);
+  for (int64_t l = first; l < n; ++l) for (int q = 0; q < 3; ++q) V[3 * l + q] -= mean[q];
+  for (int64_t l = 0; l < first; ++l) for (int q = 0; q < 3; ++q) { V[3 * l + q] = 0.0; Om[3 * l + q] = 0.0; }
+}
+
+// ---------------------------------------------------------------- state transfer kernels
+// staging layout: [n][12] = X xyz, V xyz, u xyz, Om xyz (AoS, FP64)
+__global__ void k_scatter_state(double* stage, int64_t g0, int64_t cnt, unsigned mask, int fp64, int cur, int64_t n,
+                                double* X, double* V, void* Om, int4* Kw, float4* U, double* ud, const int* topo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  const int64_t g = g0 + i;
+  const double* s = stage + 12 * i;
+  double* Xc = fp64 ? X + (size_t)cur * 3 * n : X;
+  const bool frozen = (topo[g] & F_FROZEN) != 0;
+  if (mask & 1) for (int c = 0; c < 3; ++c) Xc[c * n + g] = s[c];
+  if (mask & 2) for (int c = 0; c < 3; ++c) V[c * n + g] = frozen ? 0.0 : s[3 + c];
+  if (mask & 4) {
+    double uu[3] = {s[6], s[7], s[8]};
+    const double l2 = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+    if (fabs(l2 - 1.0) > 1e-6) {   // renormalise only inputs that are not unit already (keeps resumes exact)
+      const double l = sqrt(l2);
+      for (double& x : uu) x /= l;
+    }
+    if (fp64) {
+      double* u = ud + (size_t)cur * 3 * n;
+      for (int c = 0; c < 3; ++c) u[c * n + g] = uu[c];
+    } else {
+      U[(size_t)cur * n + g] = make_float4((float)uu[0], (float)uu[1], (float)uu[2], 0.0f);
+    }
+  }
+  if (mask & 8) {
+    for (int c = 0; c < 3; ++c) {
+      const double w = frozen ? 0.0 : s[9 + c];
+      if (fp64) ((double*)Om)[c * n + g] = w;
+      else ((float*)Om)[c * n + g] = (float)w;
+    }
+  }
+  if (!fp64 && (mask & 1)) {
+    int4 k = Kw[(size_t)cur * n + g];
+    k.x = fix32(Xc[g]); k.y = fix32(Xc[n + g]); k.z = fix32(Xc[2 * n + g]);
+    Kw[(size_t)cur * n + g] = k;
+  }
+}
+
+__global__ void k_gather_state(double* stage, int64_t g0, int64_t cnt, int fp64, int cur, int64_t n, const double* X,
+                               const double* V, const void* Om, const float4* U, const double* ud) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  const int64_t g = g0 + i;
+  double* s = stage + 12 * i;
+  const double* Xc = fp64 ? X + (size_t)cur * 3 * n : X;
+  for (int c = 0; c < 3; ++c) { s[c] = Xc[c * n + g]; s[3 + c] = V[c * n + g]; }
+  if (fp64) {
+    const double* u = ud + (size_t)cur * 3 * n;
+    for (int c = 0; c < 3; ++c) { s[6 + c] = u[c * n + g]; s[9 + c] = ((const double*)Om)[c * n + g]; }
+  } else {
+    const float4 u = U[(size_t)cur * n + g];
+    s[6] = u.x; s[7] = u.y; s[8] = u.z;
+    for (int c = 0; c < 3; ++c) s[9 + c] = ((const float*)Om)[c * n + g];
+  }
+}
+
+// ---------------------------------------------------------------- setup
+template <class Real>
+static void fill_coef(const dsdna_params& p, Coef<Real>& c) {
+  const double rc6 = std::pow(2.0, 1.0 / 6.0);
+  const double M = 2.0 * p.mass, I = 0.5 * p.mass * p.ell * p.ell;
+  c.K1 = (Real)p.K1; c.R02 = (Real)(p.R0 * p.R0); c.eps_bb = (Real)p.eps_bb;
+  c.sbb2 = (Real)(p.sigma_bb * p.sigma_bb); c.rcbb2 = (Real)(rc6 * rc6 * p.sigma_bb * p.sigma_bb);
+  c.khb = (Real)(p.K2 / (2.0 * (p.r0_hb - p.rc_hb) * (p.r0_hb - p.rc_hb)));
+  c.r0hb = (Real)p.r0_hb; c.rchb2 = (Real)(p.rc_hb * p.rc_hb);
+  c.eps = (Real)p.eps_ev;
+  c.sss2 = (Real)(p.sigma_ss * p.sigma_ss); c.rcss2 = (Real)(rc6 * rc6 * p.sigma_ss * p.sigma_ss);
+  c.scr2 = (Real)(p.sigma_cross * p.sigma_cross); c.rccr2 = (Real)(rc6 * rc6 * p.sigma_cross * p.sigma_cross);
+  c.K3 = (Real)p.K3; c.cosd = (Real)std::cos(p.d_dih); c.sind = (Real)std::sin(p.d_dih);
+  c.K4 = (Real)p.K4; c.lam = (Real)p.lambda_m; c.r0m = (Real)p.r0_m;
+  c.K5 = (Real)p.K5; c.alpha0 = (Real)p.alpha0;
+  c.K6 = (Real)p.K6;
+  c.h = (Real)(0.5 * p.ell);
+  c.dtM = (Real)(p.dt / M); c.dtI = (Real)(p.dt / I);
+  c.halfdtM = (Real)(0.5 * p.dt / M); c.halfdtI = (Real)(0.5 * p.dt / I);
+  c.M = (Real)M; c.I = (Real)I;
+  c.dt = (Real)p.dt; c.dt_d = p.dt;
+  c.gam2 = (Real)(2.0 * p.gamma); c.gamr = (Real)(p.gamma * 0.5 * p.ell * p.ell);
+  if (p.noise == DSDNA_NOISE_GAUSSIAN) {
+    c.noise_cd = std::sqrt(2.0 * p.gamma * p.kT / p.dt);
+  } else {
+    c.noise_cd = std::ldexp(std::sqrt(24.0 * p.gamma * p.kT / p.dt), -32);
+  }
+  c.noise_c = (Real)c.noise_cd;
+  const double margin = 0.01;   // absorbs FP32 rounding of the wrapped build positions
+  const double rss = rc6 * p.sigma_ss + p.skin + margin, rcr = rc6 * p.sigma_cross + p.skin + margin;
+  c.skin_half2 = (float)(0.25 * p.skin * p.skin);
+  c.rl_ss2 = (float)(rss * rss); c.rl_cr2 = (float)(rcr * rcr);
+  c.rl_max2 = (float)(std::max(rss, rcr) * std::max(rss, rcr));
+}
+
+template <class Real>
+static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
+  fill_coef(c->p, a.c);
+  a.n = c->n; a.n_mol = c->n_mol; a.nseg = c->nseg; a.cap = c->p.max_neighbors;
+  a.nsteps = 0; a.noise_mode = c->p.noise;
+  a.seed_lo = (uint32_t)c->p.seed; a.seed_hi = (uint32_t)(c->p.seed >> 32);
+  a.spin_budget = 4000000000ull;
+  a.X = c->X; a.V = c->V; a.Om = (Real*)c->Om; a.Kw = c->Kw; a.U = c->U; a.ud = c->ud;
+  a.topo = c->topo; a.img = c->img; a.kref = c->kref; a.nbr = c->nbr; a.ncnt = c->ncnt;
+  a.cnt = c->cnt; a.start = c->start; a.H = c->H; a.morton_bits = c->morton_bits; a.key = c->key;
+  a.cent = c->cent; a.wpos = c->wpos; a.bsum = c->bsum;
+  a.periodic = c->p.box[0] > 0.0 ? 1 : 0;
+  for (int k = 0; k < 3; ++k) {
+    a.nc[k] = c->nc[k];
+    a.L[k] = a.periodic ? c->p.box[k] : 0.0;
+    a.Lf[k] = (float)a.L[k];
+    a.cellh[k] = (float)(a.periodic ? c->p.box[k] / c->nc[k] : c->cellh);
+    a.Lfix[k] = (uint32_t)(uint64_t)llround(a.L[k] * 536870912.0);
+  }
+  a.mol_off = c->mol_off; a.ext = c->ext_d;
+  a.bar = c->bar; a.err = c->err; a.step = c->step_d; a.rebuild = c->rebuild; a.nrebuild = c->nrebuild;
+  a.fout = c->fout; a.eout = c->eout;
+}
+
+static int validate(const dsdna_params* p, const dsdna_system* s) {
+  if (!p || !s || s->n_mol < 1 || !s->n_bp) return fail(nullptr, DSDNA_EINVAL, "params/system missing or n_mol < 1");
+  if (s->n_mol >= (1 << 23)) return fail(nullptr, DSDNA_EINVAL, "too many molecules");
+  int64_t tot = 0;
+  for (int m = 0; m < s->n_mol; ++m) {
+    if (s->n_bp[m] < 1) return fail(nullptr, DSDNA_EINVAL, "molecule with fewer than one base pair");
+    tot += s->n_bp[m];
+  }
+  if (2 * tot >= ((int64_t)1 << 27)) return fail(nullptr, DSDNA_EINVAL, "more than 2^27 nucleotides");
+  const bool per = p->box[0] > 0.0;
+  for (int k = 0; k < 3; ++k)
+    if ((p->box[k] > 0.0) != per) return fail(nullptr, DSDNA_EINVAL, "box must be periodic in all or no directions");
+  if (!(p->dt > 0.0) || !(p->mass > 0.0) || !(p->ell > 0.0) || !(p->R0 > 0.0) || !(p->rc_hb > 0.0) || p->gamma < 0.0 || p->kT < 0.0)
+    return fail(nullptr, DSDNA_EINVAL, "non-positive dt/mass/ell/R0/rc or negative gamma/kT");
+  if (p->precision != DSDNA_PREC_MIXED && p->precision != DSDNA_PREC_FP64) return fail(nullptr, DSDNA_EINVAL, "precision");
+  if (p->noise < 0 || p->noise > 2) return fail(nullptr, DSDNA_EINVAL, "noise mode");
+  if (p->skin < 0.0) return fail(nullptr, DSDNA_EINVAL, "negative skin");
+  if (p->max_neighbors < 0 || p->max_neighbors > 64) return fail(nullptr, DSDNA_EINVAL, "max_neighbors must be <= 64");
+  if (p->block_threads && (p->block_threads < 64 || p->block_threads > 512 || p->block_threads % 32))
+    return fail(nullptr, DSDNA_EINVAL, "block_threads must be a multiple of 32 in [64, 512]");
+  if ((s->X == nullptr) != (s->u == nullptr)) return fail(nullptr, DSDNA_EINVAL, "X and u must be given together");
+  if ((s->V == nullptr) != (s->Om == nullptr)) return fail(nullptr, DSDNA_EINVAL, "V and Om must be given together");
+  return DSDNA_OK;
+}
+
+static int upload_state(dsdna_ctx* c, int64_t g0, int64_t cnt, const double* X, const double* V, const double* u,
+                        const double* Om) {
+  unsigned mask = (X ? 1u : 0u) | (V ? 2u : 0u) | (u ? 4u : 0u) | (Om ? 8u : 0u);
+  if (!mask || cnt == 0) return DSDNA_OK;
+  std::vector<double> h((size_t)cnt * 12, 0.0);
+  for (int64_t i = 0; i < cnt; ++i)
+    for (int q = 0; q < 3; ++q) {
+      if (X) h[12 * i + q] = X[3 * i + q];
+      if (V) h[12 * i + 3 + q] = V[3 * i + q];
+      if (u) h[12 * i + 6 + q] = u[3 * i + q];
+      if (Om) h[12 * i + 9 + q] = Om[3 * i + q];
+    }
+  CK(cudaMemcpyAsync(c->stage, h.data(), sizeof(double) * 12 * cnt, cudaMemcpyHostToDevice, c->st), "upload state");
+  const int cur = (int)(c->step & 1);
+  k_scatter_state<<<(unsigned)((cnt + 255) / 256), 256, 0, c->st>>>(c->stage, g0, cnt, mask, c->fp64(), cur, c->n, c->X,
+                                                                     c->V, c->Om, c->Kw, c->U, c->ud, c->topo);
+  CK(cudaGetLastError(), "scatter state");
+  CK(cudaStreamSynchronize(c->st), "upload state sync");
+  return DSDNA_OK;
+}
+
+extern "C" void dsdna_default_params(dsdna_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->K1 = 30.0; p->R0 = 0.6825; p->eps_bb = 1.0; p->sigma_bb = 0.4430;   // Table 1 backbone
+  p->K2 = 6.0; p->r0_hb = 0.0; p->rc_hb = 0.3;                            // Table 1 hydrogen bond
+  p->eps_ev = 1.0; p->sigma_ss = 1.0; p->sigma_cross = 0.5;               // Table 1 steric; Sec. 2 ghosts
+  p->K3 = 50.0; p->d_dih = -144.0 * M_PI / 180.0;                         // Table 1 dihedral
+  p->K4 = 30.0; p->lambda_m = 8.0; p->r0_m = 0.34;                        // Table 1 Morse
+  p->K5 = 200.0; p->alpha0 = 0.5 * M_PI;                                  // Table 1 planarity
+  p->K6 = 52.0;                                                           // Table 1 bending
+  p->mass = 1.0; p->ell = 0.5;                                            // Sec. 2
+  p->kT = 1.0; p->gamma = 1.0; p->dt = 0.005;                             // App. A, Eq. 16
+  p->seed = 0; p->noise = DSDNA_NOISE_UNIFORM; p->steric_phase = 0;
+  p->skin = 0.3; p->precision = DSDNA_PREC_MIXED;
+}
+
+extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys, const dsdna_allocator* alloc,
+                            void* cuda_stream, dsdna_ctx** out) {
+  if (!out) return fail(nullptr, DSDNA_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(params, sys);
+  if (rc) return rc;
+  dsdna_ctx* c = new dsdna_ctx();
+  c->p = *params;
+  if (c->p.skin == 0.0) c->p.skin = 0.3;
+  if (c->p.max_neighbors == 0) c->p.max_neighbors = 32;
+  if (c->p.block_threads == 0) c->p.block_threads = 256;
+  if (c->p.steps_per_graph <= 0) c->p.steps_per_graph = 50;
+  c->T = c->p.block_threads;
+  c->st = (cudaStream_t)cuda_stream;
+  if (alloc && alloc->alloc && alloc->release) { c->alloc = *alloc; c->have_alloc = true; }
+  auto bad = [&](int code) { g_create_error = c->errmsg; free_all(c); delete c; return code; };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return bad(fail(c, DSDNA_ECUDA, "no CUDA device"));
+  c->n_mol = sys->n_mol;
+  c->n_bp.assign(sys->n_bp, sys->n_bp + sys->n_mol);
+  c->off.assign(c->n_mol + 1, 0);
+  for (int m = 0; m < c->n_mol; ++m) { c->off[m + 1] = c->off[m] + c->n_bp[m]; c->maxN = std::max(c->maxN, c->n_bp[m]); }
+  c->n = 2 * c->off[c->n_mol];
+  c->tether.assign(c->n_mol, 0);
+  if (sys->tether) for (int m = 0; m < c->n_mol; ++m) c->tether[m] = sys->tether[m] ? 1 : 0;
+  c->ext.assign((size_t)c->n_mol * 8, 0.0);
+  const int64_t n = c->n;
+  c->nseg = (n + c->T - 1) / c->T;
+
+  // cell table: Morton index of the wrapped cell in a periodic box, hash otherwise
+  const double rc6 = std::pow(2.0, 1.0 / 6.0);
+  const double rmax = rc6 * std::max(c->p.sigma_ss, c->p.sigma_cross) + c->p.skin + 0.01;
+  c->cellh = rmax * 1.0001;
+  if (c->p.box[0] > 0.0) {
+    int bits = 1;
+    for (int k = 0; k < 3; ++k) {
+      c->nc[k] = (int)std::floor(c->p.box[k] / c->cellh);
+      if (c->nc[k] < 1) return bad(fail(c, DSDNA_EINVAL, "periodic box smaller than the interaction range"));
+      if (c->nc[k] > 1024) return bad(fail(c, DSDNA_EINVAL, "periodic box wider than 1024 cells"));
+      while ((1 << bits) < c->nc[k]) ++bits;
+    }
+    c->morton_bits = bits;
+    c->H = 1u << (3 * bits);
+  } else {
+    unsigned H = 1024;
+    while ((int64_t)H < 2 * n) H <<= 1;
+    c->H = H;
+    c->morton_bits = 0;
+  }
+
+  // allocations
+  const bool f64 = c->fp64();
+  const size_t nn = (size_t)n;
+#define ALLOC(ptr, type, count)                                                              \
+  do {                                                                                       \
+    c->ptr = (type*)dalloc(c, sizeof(type) * (size_t)(count));                               \
+    if (!c->ptr) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: " #ptr));       \
+  } while (0)
+  ALLOC(X, double, (f64 ? 6 : 3) * nn);
+  ALLOC(V, double, 3 * nn);
+  c->Om = dalloc(c, (f64 ? 8 : 4) * 3 * nn);
+  if (!c->Om) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: Om"));
+  if (f64) { ALLOC(ud, double, 6 * nn); } else { ALLOC(Kw, int4, 2 * nn); ALLOC(U, float4, 2 * nn); }
+  ALLOC(topo, int, nn); ALLOC(img, int, nn); ALLOC(kref, int, 3 * nn);
+  ALLOC(nbr, int, (size_t)c->p.max_neighbors * nn); ALLOC(ncnt, int, nn);
+  ALLOC(cnt, unsigned, c->H); ALLOC(start, unsigned, (size_t)c->H + 1); ALLOC(key, int, nn);
+  ALLOC(cent, float4, nn); ALLOC(wpos, float4, nn);
+  ALLOC(mol_off, int64_t, c->n_mol + 1); ALLOC(ext_d, double, (size_t)c->n_mol * 8);
+  ALLOC(bar, GridBar, 1); ALLOC(err, unsigned, 4); ALLOC(step_d, int64_t, 1); ALLOC(rebuild, int, 4);
+  ALLOC(nrebuild, unsigned long long, 1);
+  ALLOC(fout, double, 6 * nn); ALLOC(eout, double, (size_t)c->n_mol * EOUT_STRIDE);
+  ALLOC(stage, double, 12 * nn);
+  ALLOC(obs_scratch, double, 3 * (size_t)(3 * (c->maxN + 4)));
+  ALLOC(obs_out, double, 8);
+#undef ALLOC
+  // launch shape per mode (cooperative: every CTA resident)
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  for (int mode = 0; mode < 3; ++mode) {
+    int bps = 0;
+    cudaError_t e = f64 ? engine_occupancy<double>(mode, c->T, &bps, &c->smem[mode])
+                        : engine_occupancy<float>(mode, c->T, &bps, &c->smem[mode]);
+    if (e != cudaSuccess || bps < 1) return bad(fail(c, DSDNA_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e)));
+    if (c->p.blocks_per_sm > 0) bps = std::min(bps, c->p.blocks_per_sm);
+    c->grid[mode] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * nsm, c->nseg));
+  }
+  c->bsum = (unsigned*)dalloc(c, sizeof(unsigned) * (size_t)std::max(c->grid[0], std::max(c->grid[1], c->grid[2])));
+  if (!c->bsum) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: bsum"));
+
+  // topology flags (Sec. 2; anchored and loaded base pairs of Sec. 4)
+  std::vector<int> topo(nn);
+  for (int m = 0; m < c->n_mol; ++m) {
+    const int N = c->n_bp[m];
+    for (int k = 0; k < N; ++k)
+      for (int s = 0; s < 2; ++s) {
+        const int64_t g = 2 * (c->off[m] + k) + s;
+        const int q = s == 0 ? k : N - 1 - k;     // index along the strand from its 5' end
+        int f = 0;
+        if (q % 3 == c->p.steric_phase) f |= F_STERIC;
+        if (q > 0) f |= F_PREV;
+        if (q < N - 1) f |= F_NEXT;
+        if (c->tether[m] && k == 0) f |= F_FROZEN;
+        if (k == N - 1) f |= F_TOP;
+        topo[g] = f | (m << 8);
+      }
+  }
+  auto cpy = [&](void* dst, const void* src, size_t b) { return cudaMemcpy(dst, src, b, cudaMemcpyHostToDevice); };
+  if (cpy(c->topo, topo.data(), sizeof(int) * nn) != cudaSuccess ||
+      cpy(c->mol_off, c->off.data(), sizeof(int64_t) * (c->n_mol + 1)) != cudaSuccess ||
+      cpy(c->ext_d, c->ext.data(), sizeof(double) * c->ext.size()) != cudaSuccess)
+    return bad(fail(c, DSDNA_ECUDA, "topology upload"));
+  if (cudaMemset(c->cnt, 0, sizeof(unsigned) * c->H) != cudaSuccess || cudaMemset(c->err, 0, 16) != cudaSuccess ||
+      cudaMemset(c->step_d, 0, 8) != cudaSuccess || cudaMemset(c->nrebuild, 0, 8) != cudaSuccess ||
+      cudaMemset(c->bar, 0, sizeof(GridBar)) != cudaSuccess || cudaMemset(c->ncnt, 0, sizeof(int) * nn) != cudaSuccess ||
+      cudaMemset(c->Om, 0, (f64 ? 8 : 4) * 3 * nn) != cudaSuccess || cudaMemset(c->V, 0, 24 * nn) != cudaSuccess)
+    return bad(fail(c, DSDNA_ECUDA, "initialisation"));
+  if (!f64 && cudaMemset(c->Kw, 0, sizeof(int4) * 2 * nn) != cudaSuccess) return bad(fail(c, DSDNA_ECUDA, "initialisation"));
+  const int one = 1;
+  if (cpy(c->rebuild, &one, sizeof(int)) != cudaSuccess) return bad(fail(c, DSDNA_ECUDA, "initialisation"));
+  fill_args(c, c->kf);
+  fill_args(c, c->kd);
+
+  // initial state
+  std::vector<double> Xh, uh, Vh, Oh;
+  const double *X0 = sys->X, *u0 = sys->u, *V0 = sys->V, *O0 = sys->Om;
+  if (!X0) {
+    Xh.resize(3 * nn); uh.resize(3 * nn);
+    for (int m = 0; m < c->n_mol; ++m) host_helix(c->p, c->n_bp[m], &Xh[6 * c->off[m]], &uh[6 * c->off[m]]);
+    X0 = Xh.data(); u0 = uh.data();
+  }
+  if (!V0) {
+    Vh.resize(3 * nn); Oh.resize(3 * nn);
+    for (int m = 0; m < c->n_mol; ++m)
+      host_maxwell(c->p, m, c->n_bp[m], u0 + 6 * c->off[m], c->tether[m], &Vh[6 * c->off[m]], &Oh[6 * c->off[m]]);
+    V0 = Vh.data(); O0 = Oh.data();
+  }
+  rc = upload_state(c, 0, n, X0, V0, u0, O0);
+  if (rc) return bad(rc);
+  *out = c;
+  return DSDNA_OK;
+}
+
+// ---------------------------------------------------------------- launches
+static int launch(dsdna_ctx* c, int mode, int64_t nsteps) {
+  CK(cudaMemsetAsync(c->bar, 0, sizeof(GridBar), c->st), "barrier reset");
+  cudaError_t e;
+  if (c->fp64()) {
+    KArgs<double> a = c->kd;
+    a.nsteps = nsteps;
+    e = engine_launch<double>(mode, a, c->grid[mode], c->T, c->smem[mode], c->st);
+  } else {
+    KArgs<float> a = c->kf;
+    a.nsteps = nsteps;
+    e = engine_launch<float>(mode, a, c->grid[mode], c->T, c->smem[mode], c->st);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "engine launch");
+  return DSDNA_OK;
+}
+
+static int map_err(dsdna_ctx* c, unsigned bits) {
+  if (!bits) return DSDNA_OK;
+  c->poisoned = true;
+  if (bits & B_EFENE) return fail(c, DSDNA_EFENE, "backbone bond reached R0 (FENE diverges)");
+  if (bits & B_ENAN) return fail(c, DSDNA_ENAN, "non-finite velocity");
+  if (bits & B_EOVF) return fail(c, DSDNA_EOVERFLOW, "neighbour list capacity exceeded");
+  if (bits & B_EIMG) return fail(c, DSDNA_EOVERFLOW, "periodic image index out of range");
+  if (bits & B_ETIMEOUT) return fail(c, DSDNA_ETIMEOUT, "device barrier timed out");
+  return fail(c, DSDNA_ECUDA, "unknown device error");
+}
+
+static int sync_check(dsdna_ctx* c) {
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  unsigned bits = 0;
+  CK(cudaMemcpy(&bits, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error word");
+  return map_err(c, bits);
+}
+
+extern "C" int dsdna_set_external_force_torque(dsdna_ctx* c, int mol, const double f[3], const double t[3]) {
+  if (!c) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  if (mol < -1 || mol >= c->n_mol) return fail(c, DSDNA_EINVAL, "molecule index out of range");
+  const int m0 = mol < 0 ? 0 : mol, m1 = mol < 0 ? c->n_mol : mol + 1;
+  for (int m = m0; m < m1; ++m)
+    for (int q = 0; q < 3; ++q) {
+      c->ext[8 * m + q] = f ? f[q] : 0.0;
+      c->ext[8 * m + 3 + q] = t ? t[q] : 0.0;
+    }
+  CK(cudaMemcpyAsync(c->ext_d + 8 * m0, c->ext.data() + 8 * m0, sizeof(double) * 8 * (m1 - m0), cudaMemcpyHostToDevice,
+                     c->st), "upload load");
+  CK(cudaStreamSynchronize(c->st), "upload load sync");
+  return DSDNA_OK;
+}
+
+extern "C" int dsdna_step(dsdna_ctx* c, int64_t nsteps) {
+  if (!c) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  if (nsteps < 0) return fail(c, DSDNA_EINVAL, "negative step count");
+  const int64_t K = c->p.steps_per_graph;
+  while (nsteps > 0) {
+    const int64_t chunk = std::min(nsteps, K);
+    if (chunk == K && !c->graph_failed) {
+      if (!c->gexec) {
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          const int rc = launch(c, MODE_STEP, K);
+          cudaError_t e2 = cudaStreamEndCapture(c->st, &g);
+          ok = (rc == DSDNA_OK) && e2 == cudaSuccess && g != nullptr;
+          if (ok) ok = cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess;
+          if (g) cudaGraphDestroy(g);
+          c->poisoned = false;
+          c->errmsg.clear();
+        }
+        if (!ok) { c->graph_failed = true; c->gexec = nullptr; cudaGetLastError(); }
+      }
+      if (c->gexec) {
+        CK(cudaGraphLaunch(c->gexec, c->st), "graph launch");
+        c->step += chunk;
+        nsteps -= chunk;
+        continue;
+      }
+    }
+    int rc = launch(c, MODE_STEP, chunk);
+    if (rc) return rc;
+    c->step += chunk;
+    nsteps -= chunk;
+  }
+  return DSDNA_OK;
+}
+
+extern "C" int dsdna_synchronize(dsdna_ctx* c) {
+  if (!c) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  return sync_check(c);
+}
+
+extern "C" int dsdna_energy_virial(dsdna_ctx* c, int mol, double energy[DSDNA_NTERMS], double virial[6]) {
+  if (!c) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  if (mol < -1 || mol >= c->n_mol) return fail(c, DSDNA_EINVAL, "molecule index out of range");
+  CK(cudaMemsetAsync(c->eout, 0, sizeof(double) * EOUT_STRIDE * c->n_mol, c->st), "clear energies");
+  int rc = launch(c, MODE_ENERGY, 0);
+  if (rc) return rc;
+  rc = sync_check(c);
+  if (rc) return rc;
+  std::vector<double> e((size_t)c->n_mol * EOUT_STRIDE);
+  CK(cudaMemcpy(e.data(), c->eout, sizeof(double) * e.size(), cudaMemcpyDeviceToHost), "read energies");
+  const int m0 = mol < 0 ? 0 : mol, m1 = mol < 0 ? c->n_mol : mol + 1;
+  for (int k = 0; k < DSDNA_NTERMS; ++k) if (energy) energy[k] = 0.0;
+  for (int k = 0; k < 6; ++k) if (virial) virial[k] = 0.0;
+  for (int m = m0; m < m1; ++m) {
+    for (int k = 0; k < DSDNA_NTERMS; ++k) if (energy) energy[k] += e[(size_t)m * EOUT_STRIDE + k];
+    for (int k = 0; k < 6; ++k) if (virial) virial[k] += e[(size_t)m * EOUT_STRIDE + NTERMS + k];
+  }
+  return DSDNA_OK;
+}
+
+extern "C" int dsdna_observables(dsdna_ctx* c, int mol, unsigned flags, dsdna_obs* out) {
+  if (!c || !out) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  if (mol < 0 || mol >= c->n_mol) return fail(c, DSDNA_EINVAL, "molecule index out of range");
+  int rc = sync_check(c);
+  if (rc) return rc;
+  const int cur = (int)(c->step & 1);
+  ObsArgs a{};
+  a.n = c->n;
+  a.X = c->fp64() ? c->X + (size_t)cur * 3 * c->n : c->X;
+  a.uf = c->fp64() ? nullptr : c->U + (size_t)cur * c->n;
+  a.ud = c->fp64() ? c->ud + (size_t)cur * 3 * c->n : nullptr;
+  a.g0 = 2 * c->off[mol];
+  a.N = c->n_bp[mol];
+  a.h = 0.5 * c->p.ell;
+  a.rc2 = c->p.rc_hb * c->p.rc_hb;
+  a.mid = c->obs_scratch;
+  a.ca = a.mid + 3 * (size_t)(c->maxN + 4);
+  a.cb = a.ca + 3 * (size_t)(c->maxN + 4);
+  a.out = c->obs_out;
+  CK(obs_launch(a, flags, c->st), "observables");
+  double o[8];
+  CK(cudaMemcpyAsync(o, c->obs_out, sizeof(o), cudaMemcpyDeviceToHost, c->st), "read observables");
+  CK(cudaStreamSynchronize(c->st), "observables sync");
+  out->rz = o[0];
+  out->denat = o[1] / (double)a.N;
+  out->tw = o[2];
+  out->tw_ideal = a.N >= 3 ? (double)(a.N - 2) * (c->p.d_dih + M_PI) / (2.0 * M_PI) : 0.0;
+  out->lk = (flags & DSDNA_OBS_LK) ? o[4] : 0.0;
+  out->wr = (flags & DSDNA_OBS_LK) ? o[4] - o[2] : 0.0;
+  return DSDNA_OK;
+}
+
+extern "C" int dsdna_get_state(dsdna_ctx* c, int mol, double* X, double* V, double* u, double* Om) {
+  if (!c) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  if (mol < -1 || mol >= c->n_mol) return fail(c, DSDNA_EINVAL, "molecule index out of range");
+  int rc = sync_check(c);
+  if (rc) return rc;
+  const int64_t g0 = mol < 0 ? 0 : 2 * c->off[mol];
+  const int64_t cnt = mol < 0 ? c->n : 2 * (int64_t)c->n_bp[mol];
+  const int cur = (int)(c->step & 1);
+  k_gather_state<<<(unsigned)((cnt + 255) / 256), 256, 0, c->st>>>(c->stage, g0, cnt, c->fp64(), cur, c->n, c->X, c->V,
+                                                                    c->Om, c->U, c->ud);
+  CK(cudaGetLastError(), "gather state");
+  std::vector<double> h((size_t)cnt * 12);
+  CK(cudaMemcpyAsync(h.data(), c->stage, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st), "download state");
+  CK(cudaStreamSynchronize(c->st), "download sync");
+  for (int64_t i = 0; i < cnt; ++i)
+    for (int q = 0; q < 3; ++q) {
+      if (X) X[3 * i + q] = h[12 * i + q];
+      if (V) V[3 * i + q] = h[12 * i + 3 + q];
+      if (u) u[3 * i + q] = h[12 * i + 6 + q];
+      if (Om) Om[3 * i + q] = h[12 * i + 9 + q];
+    }
+  return DSDNA_OK;
+}
+
+extern "C" int dsdna_set_state(dsdna_ctx* c, int mol, const double* X, const double* V, const double* u, const double* Om) {
+  if (!c) return DSDNA_EINVAL;
+  if (mol < -1 || mol >= c->n_mol) return fail(c, DSDNA_EINVAL, "molecule index out of range");
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_state sync");
+  c->poisoned = false;
+  c->errmsg.clear();
+  CK(cudaMemsetAsync(c->err, 0, 16, c->st), "clear errors");
+  const int one = 1;
+  CK(cudaMemcpyAsync(c->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, c->st), "request rebuild");
+  const int64_t g0 = mol < 0 ? 0 : 2 * c->off[mol];
+  const int64_t cnt = mol < 0 ? c->n : 2 * (int64_t)c->n_bp[mol];
+  return upload_state(c, g0, cnt, X, V, u, Om);
+}
+
+extern "C" int dsdna_compute_forces(dsdna_ctx* c, double* Fb, double* Fp) {
+  if (!c) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  int rc = launch(c, MODE_FORCES, 0);
+  if (rc) return rc;
+  rc = sync_check(c);
+  if (rc) return rc;
+  std::vector<double> h((size_t)c->n * 6);
+  CK(cudaMemcpy(h.data(), c->fout, sizeof(double) * h.size(), cudaMemcpyDeviceToHost), "read forces");
+  for (int64_t i = 0; i < c->n; ++i)
+    for (int q = 0; q < 3; ++q) {
+      if (Fb) Fb[3 * i + q] = h[6 * i + q];
+      if (Fp) Fp[3 * i + q] = h[6 * i + 3 + q];
+    }
+  return DSDNA_OK;
+}
+
+extern "C" int dsdna_neighbor_pairs(dsdna_ctx* c, int64_t cap, int64_t* pi, int64_t* pj, int64_t* count) {
+  if (!c || !count) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  const int one = 1;
+  CK(cudaMemcpyAsync(c->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, c->st), "request rebuild");
+  int rc = launch(c, MODE_FORCES, 0);
+  if (rc) return rc;
+  rc = sync_check(c);
+  if (rc) return rc;
+  const size_t nn = (size_t)c->n;
+  std::vector<int> nb((size_t)c->p.max_neighbors * nn), nc(nn);
+  CK(cudaMemcpy(nb.data(), c->nbr, sizeof(int) * nb.size(), cudaMemcpyDeviceToHost), "read list");
+  CK(cudaMemcpy(nc.data(), c->ncnt, sizeof(int) * nc.size(), cudaMemcpyDeviceToHost), "read counts");
+  int64_t k = 0;
+  for (size_t i = 0; i < nn; ++i)
+    for (int q = 0; q < nc[i]; ++q) {
+      const int64_t j = nb[(size_t)q * nn + i] & ((1 << NBR_J_BITS) - 1);
+      if ((int64_t)i < j) {
+        if (k < cap) { pi[k] = (int64_t)i; pj[k] = j; }
+        ++k;
+      }
+    }
+  *count = k;
+  return DSDNA_OK;
+}
+
+extern "C" int dsdna_get_info(const dsdna_ctx* c, dsdna_info* info) {
+  if (!c || !info) return DSDNA_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  info->n_nt = c->n;
+  info->n_mol = c->n_mol;
+  info->step = c->step;
+  unsigned long long nb = 0;
+  cudaStreamSynchronize(c->st);
+  cudaMemcpy(&nb, c->nrebuild, sizeof(nb), cudaMemcpyDeviceToHost);
+  info->rebuilds = (int64_t)nb;
+  info->grid_blocks = c->grid[MODE_STEP];
+  info->block_threads = c->T;
+  info->max_neighbors = c->p.max_neighbors;
+  info->precision = c->p.precision;
+  info->skin = c->p.skin;
+  info->cell_table = c->H;
+  info->device_bytes = c->bytes;
+  return DSDNA_OK;
+}
+
+extern "C" int64_t dsdna_step_counter(const dsdna_ctx* c) { return c ? c->step : -1; }
+
+extern "C" const char* dsdna_last_error(const dsdna_ctx* c) {
+  return c ? c->errmsg.c_str() : g_create_error.c_str();
+}
+
+extern "C" void dsdna_destroy(dsdna_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  free_all(c);
+  delete c;
+}

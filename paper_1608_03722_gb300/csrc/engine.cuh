@@ -1,0 +1,381 @@
+// engine.cuh -- device side of the dsDNA engine (sm_103a).
+//
+// One persistent cooperative kernel advances the single-nucleotide dsDNA
+// model of Fosado et al. (arXiv:1608.03722): per step it evaluates every
+// interaction of App. A (Eqs. 9-15, Table 1) on chain segments staged in
+// shared memory, adds the typed WCA pairs of a full neighbour list, applies
+// the loads of Sec. 4, and integrates App. A Eq. 8 with the step of Eq. 16.
+// The cell/neighbour rebuild runs inside the same kernel between bounded grid
+// barriers when a bead moved more than skin/2.
+//
+// Precision (Real = float, "mixed"): the FP64 centre positions X and
+// velocities V are the integrator's accumulators; forces, orientation u and
+// angular velocity are FP32.  Displacements between nucleotides come from a
+// fixed-point mirror of X (low 32 bits of round(X * 2^29)): the difference of
+// two mirrors is exact for separations below 4 nm, so no FP64 subtraction is
+// needed in the force loops.  Real = double runs every step in FP64.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dsdna {
+
+// ---------------------------------------------------------------- constants
+enum : int { F_STERIC = 1, F_PREV = 2, F_NEXT = 4, F_FROZEN = 8, F_TOP = 16 };
+enum : unsigned {
+  B_STALE = 1u, B_EFENE = 2u, B_ENAN = 4u, B_EOVF = 8u, B_ETIMEOUT = 16u, B_EIMG = 32u
+};
+constexpr unsigned B_ERRMASK = B_EFENE | B_ENAN | B_EOVF | B_ETIMEOUT | B_EIMG;
+enum : int { MODE_STEP = 0, MODE_FORCES = 1, MODE_ENERGY = 2 };
+constexpr int NTERMS = 10;
+constexpr int EOUT_STRIDE = 16;           // energy terms + 6 virial
+constexpr float FIX_SCALE_F = 1.0f / 536870912.0f;  // 2^-29
+constexpr double FIX_SCALE_D = 1.0 / 536870912.0;
+constexpr int NBR_J_BITS = 27;
+
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+  unsigned acc[3];
+  unsigned pad[3];
+};
+
+template <class Real>
+struct Coef {
+  Real K1, R02, eps_bb, sbb2, rcbb2;
+  Real khb, r0hb, rchb2;
+  Real eps, sss2, rcss2, scr2, rccr2;
+  Real K3, cosd, sind;
+  Real K4, lam, r0m;
+  Real K5, alpha0;
+  Real K6;
+  Real h;            // ell / 2
+  Real dtM, dtI;     // dt / M, dt / I
+  Real dt;
+  Real gam2, gamr;   // 2 gamma, gamma ell^2 / 2
+  Real noise_c;      // uniform: sqrt(24 gamma kT/dt) 2^-32; gaussian: sqrt(2 gamma kT/dt)
+  Real halfdtM, halfdtI;
+  Real M, I;
+  float skin_half2;  // (skin/2)^2
+  float rl_ss2, rl_cr2, rl_max2;
+  double dt_d;       // FP64 step for the position accumulation
+  double noise_cd;   // FP64 copy of noise_c
+};
+
+template <class Real>
+struct KArgs {
+  Coef<Real> c;
+  int64_t n;
+  int n_mol;
+  int64_t nseg;
+  int cap;
+  int64_t nsteps;
+  int noise_mode;
+  uint32_t seed_lo, seed_hi;
+  unsigned long long spin_budget;
+  // state
+  double* X;       // mixed: [3][n]; fp64: [2][3][n]
+  double* V;       // [3][n]
+  Real* Om;        // [3][n]
+  int4* Kw;        // mixed: [2][n] fixed-point mirror (w = packed image)
+  float4* U;       // mixed: [2][n] orientation (w unused)
+  double* ud;      // fp64: [2][3][n] orientation
+  const int* topo; // [n] flags | mol << 8
+  int* img;        // [n] packed image (both modes)
+  int* kref;       // [3][n] mirror at the last build
+  int* nbr;        // [cap][n] (j | image code << 27)
+  int* ncnt;       // [n]
+  // cell hash
+  unsigned* cnt;   // [H]
+  unsigned* start; // [H + 1]
+  unsigned H;
+  int morton_bits; // > 0: periodic Morton index with that many bits per axis
+  int* key;        // [n]
+  float4* cent;    // [n] cell-sorted (position, slot)
+  float4* wpos;    // [n] wrapped bead position, w = molecule
+  unsigned* bsum;  // [grid]
+  int periodic;
+  int nc[3];
+  float cellh[3];
+  float Lf[3];
+  double L[3];
+  unsigned Lfix[3];
+  // molecules
+  const int64_t* mol_off;  // [n_mol + 1] base-pair offsets
+  const double* ext;       // [n_mol][8]: f xyz, torque xyz
+  // control
+  GridBar* bar;
+  unsigned* err;
+  int64_t* step;
+  int* rebuild;
+  unsigned long long* nrebuild;
+  // outputs
+  double* fout;    // MODE_FORCES: [n][6]
+  double* eout;    // MODE_ENERGY: [n_mol][16]
+};
+
+// ---------------------------------------------------------------- small vectors
+template <class R>
+struct V3 {
+  R x, y, z;
+};
+template <class R> __device__ __forceinline__ V3<R> mk(R x, R y, R z) { return V3<R>{x, y, z}; }
+template <class R> __device__ __forceinline__ V3<R> operator+(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class R> __device__ __forceinline__ V3<R> operator-(V3<R> a, V3<R> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class R> __device__ __forceinline__ V3<R> operator-(V3<R> a) { return {-a.x, -a.y, -a.z}; }
+template <class R> __device__ __forceinline__ V3<R> operator*(R s, V3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <class R> __device__ __forceinline__ void operator+=(V3<R>& a, V3<R> b) { a.x += b.x; a.y += b.y; a.z += b.z; }
+template <class R> __device__ __forceinline__ void operator-=(V3<R>& a, V3<R> b) { a.x -= b.x; a.y -= b.y; a.z -= b.z; }
+template <class R> __device__ __forceinline__ R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class R> __device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float log_(float x) { return logf(x); }
+__device__ __forceinline__ double log_(double x) { return log(x); }
+__device__ __forceinline__ float exp_(float x) { return expf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+__device__ __forceinline__ float acos_(float x) { return acosf(x); }
+__device__ __forceinline__ double acos_(double x) { return acos(x); }
+__device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ void sincos_(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sincos_(double a, double* s, double* c) { sincos(a, s, c); }
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Counter-based generator of Salmon et al. (SC'11): ten rounds, multipliers
+// 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a = c.x, b = c.z;
+    const uint32_t hi_a = __umulhi(0xD2511F53u, a), lo_a = 0xD2511F53u * a;
+    const uint32_t hi_b = __umulhi(0xCD9E8D57u, b), lo_b = 0xCD9E8D57u * b;
+    c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// One site's Langevin noise (App. A Eq. 8): counter (local nucleotide, step,
+// 2*mol + site), key = seed.
+template <class Real>
+__device__ __forceinline__ V3<Real> site_noise(const KArgs<Real>& a, uint32_t local, int64_t step, int mol, int site) {
+  if (a.noise_mode == 0) return V3<Real>{0, 0, 0};
+  uint4 r = philox10(make_uint4(local, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)(2 * mol + site)),
+                     a.seed_lo, a.seed_hi);
+  if (a.noise_mode == 1) {
+    if constexpr (sizeof(Real) == 8) {
+      const double cc = a.c.noise_cd;
+      return V3<Real>{((double)r.x - 2147483647.5) * cc, ((double)r.y - 2147483647.5) * cc,
+                      ((double)r.z - 2147483647.5) * cc};
+    } else {
+      const float cc = a.c.noise_c;
+      return V3<Real>{((float)(int)(r.x ^ 0x80000000u) + 0.5f) * cc, ((float)(int)(r.y ^ 0x80000000u) + 0.5f) * cc,
+                      ((float)(int)(r.z ^ 0x80000000u) + 0.5f) * cc};
+    }
+  }
+  // Gaussian (Box-Muller)
+  const Real s32 = (Real)(1.0 / 4294967296.0);
+  Real u0 = ((Real)r.x + (Real)0.5) * s32, u1 = ((Real)r.y + (Real)0.5) * s32;
+  Real u2 = ((Real)r.z + (Real)0.5) * s32, u3 = ((Real)r.w + (Real)0.5) * s32;
+  Real r0 = sqrt_((Real)-2 * log_(u0)), r1 = sqrt_((Real)-2 * log_(u2));
+  Real s0, c0, s1, c1;
+  sincos_((Real)6.283185307179586 * u1, &s0, &c0);
+  sincos_((Real)6.283185307179586 * u3, &s1, &c1);
+  const Real cc = a.c.noise_c;
+  return V3<Real>{cc * r0 * c0, cc * r0 * s0, cc * r1 * c1};
+}
+
+// ---------------------------------------------------------------- positions
+// Slot data staged in shared memory.
+template <class Real> struct SPos;
+template <> struct SPos<float> { int kx, ky, kz; float ux, uy, uz; };
+template <> struct SPos<double> { double x, y, z, ux, uy, uz; };
+
+__device__ __forceinline__ float fixdiff(int a, int b) {   // (b - a) in nm, exact wrap-around difference
+  return (float)(int)((unsigned)b - (unsigned)a) * FIX_SCALE_F;
+}
+__device__ __forceinline__ V3<float> rel(const SPos<float>& o, const SPos<float>& b) {
+  return V3<float>{fixdiff(o.kx, b.kx), fixdiff(o.ky, b.ky), fixdiff(o.kz, b.kz)};
+}
+__device__ __forceinline__ V3<double> rel(const SPos<double>& o, const SPos<double>& b) {
+  return V3<double>{b.x - o.x, b.y - o.y, b.z - o.z};
+}
+template <class Real> __device__ __forceinline__ V3<Real> uvec(const SPos<Real>& s) { return V3<Real>{s.ux, s.uy, s.uz}; }
+
+// low 32 bits of round(x * 2^29): the exponent of 1.5 * 2^52 + x 2^29 puts
+// the integer part in the low mantissa bits (|x| < 2^22 nm)
+__device__ __forceinline__ int fix32(double x) {
+  const double t = fma(x, 536870912.0, 6755399441055744.0);
+  return (int)(unsigned)__double_as_longlong(t);
+}
+
+// bead offset -h u on the fixed-point grid (rebuild trigger only)
+__device__ __forceinline__ int bead_off(float hu) { return __float2int_rn(-hu * 536870912.0f); }
+
+template <class Real>
+__device__ __forceinline__ void load_slot(const KArgs<Real>& a, int cur, int64_t g, SPos<Real>& s) {
+  if constexpr (sizeof(Real) == 4) {
+    const int4 k = a.Kw[(size_t)cur * a.n + g];
+    const float4 u = a.U[(size_t)cur * a.n + g];
+    s.kx = k.x; s.ky = k.y; s.kz = k.z;
+    s.ux = u.x; s.uy = u.y; s.uz = u.z;
+  } else {
+    const double* X = a.X + (size_t)cur * 3 * a.n;
+    const double* u = a.ud + (size_t)cur * 3 * a.n;
+    s.x = X[g]; s.y = X[a.n + g]; s.z = X[2 * a.n + g];
+    s.ux = u[g]; s.uy = u[a.n + g]; s.uz = u[2 * a.n + g];
+  }
+}
+
+__device__ __forceinline__ int img_comp(int packed, int c) {
+  return ((int)((unsigned)packed << (22 - 10 * c))) >> 22;   // signed 10-bit field c
+}
+
+// ---------------------------------------------------------------- interaction terms
+// Each returns the force on the second site (first gets the opposite) or the
+// forces on all sites, and the energy when E != nullptr.
+
+// App. A Eq. 9 + Table 1 backbone WCA: d = b_next - b_this.
+template <class Real>
+__device__ __forceinline__ V3<Real> t_fene(const Coef<Real>& c, V3<Real> d, unsigned& fl, Real* E) {
+  Real r2 = dot(d, d);
+  if (r2 >= c.R02) { fl |= B_EFENE; r2 = (Real)0.98 * c.R02; }
+  const Real q = (Real)1 - r2 / c.R02;
+  Real fr = -c.K1 / q;
+  Real e = (Real)0, ew = (Real)0;
+  if (E) e = (Real)-0.5 * c.K1 * c.R02 * log_(q);
+  if (r2 < c.rcbb2) {
+    const Real s2 = c.sbb2 / r2, s6 = s2 * s2 * s2;
+    fr += (Real)24 * c.eps_bb * s6 * ((Real)2 * s6 - (Real)1) / r2;
+    if (E) ew = (Real)4 * c.eps_bb * (s6 * s6 - s6 + (Real)0.25);
+  }
+  if (E) { E[0] += e; E[1] += ew; }
+  return fr * d;
+}
+
+// App. A Eq. 13: d = p_next - p_this.
+template <class Real>
+__device__ __forceinline__ V3<Real> t_morse(const Coef<Real>& c, V3<Real> d, Real* E) {
+  const Real r = sqrt_(dot(d, d));
+  const Real x = exp_(-c.lam * (r - c.r0m));
+  if (E) E[5] += c.K4 * ((Real)1 - x) * ((Real)1 - x);
+  // force on the second site: -dU/dr * d / r
+  return ((Real)-2 * c.K4 * c.lam * x * ((Real)1 - x) / r) * d;
+}
+
+// App. A Eq. 12 on A-E-F-B (positions relative to anything).  phi with the
+// IUPAC sign; forces written with p = b1.b2/|b2|^2, q = b3.b2/|b2|^2.
+template <class Real>
+__device__ __forceinline__ void t_dihedral(const Coef<Real>& c, V3<Real> A, V3<Real> Ep, V3<Real> Fp, V3<Real> B,
+                                           V3<Real>& fA, V3<Real>& fE, V3<Real>& fF, V3<Real>& fB, Real* E) {
+  const V3<Real> b1 = Ep - A, b2 = Fp - Ep, b3 = B - Fp;
+  const V3<Real> n1 = cross(b1, b2), n2 = cross(b2, b3);
+  const Real n1s = dot(n1, n1), n2s = dot(n2, n2), b2s = dot(b2, b2);
+  const Real lb2 = sqrt_(b2s);
+  const Real y = lb2 * dot(b1, n2), x = dot(n1, n2);
+  // sin(phi - d) and cos(phi - d) from (x, y) without the angle itself
+  const Real inv = rsqrt_(x * x + y * y);
+  const Real cp = x * inv, sp = y * inv;
+  const Real s_pd = sp * c.cosd - cp * c.sind;   // sin(phi - d)
+  if (E) E[4] += c.K3 * ((Real)1 + (cp * c.cosd + sp * c.sind));
+  const Real dU = -c.K3 * s_pd;                  // dU/dphi
+  fA = (dU * lb2 / n1s) * n1;                    // -dU * (-|b2|/|n1|^2 n1)
+  fB = (-dU * lb2 / n2s) * n2;                   // -dU * (|b2|/|n2|^2 n2)
+  const Real p = dot(b1, b2) / b2s, q = dot(b3, b2) / b2s;
+  fE = ((Real)-1 - p) * fA + q * fB;
+  fF = p * fA - ((Real)1 + q) * fB;
+}
+
+// App. A Eq. 14: angle at vertex V between ends P (= E, patch i) and Q (= B, bead i+1).
+template <class Real>
+__device__ __forceinline__ void t_planar(const Coef<Real>& c, V3<Real> v1, V3<Real> v2, V3<Real>& f1, V3<Real>& f2,
+                                         Real* E) {
+  const Real i1 = rsqrt_(dot(v1, v1)), i2 = rsqrt_(dot(v2, v2));
+  const V3<Real> e1 = i1 * v1, e2 = i2 * v2;
+  Real cs = dot(e1, e2);
+  cs = cs > (Real)1 ? (Real)1 : (cs < (Real)-1 ? (Real)-1 : cs);
+  const Real al = acos_(cs);
+  Real sn = sqrt_((Real)1 - cs * cs);
+  if (sn < (Real)1e-6) sn = (Real)1e-6;
+  if (E) E[6] += (Real)0.5 * c.K5 * (al - c.alpha0) * (al - c.alpha0);
+  const Real k = c.K5 * (al - c.alpha0) / sn;    // dU/dalpha / sin(alpha)
+  f1 = (k * i1) * (e2 - cs * e1);
+  f2 = (k * i2) * (e1 - cs * e2);
+}
+
+// App. A Eq. 15 at vertex patch i between patches i-1 (v1) and i+1 (v2).
+template <class Real>
+__device__ __forceinline__ void t_bend(const Coef<Real>& c, V3<Real> v1, V3<Real> v2, V3<Real>& f1, V3<Real>& f2,
+                                       Real* E) {
+  const Real i1 = rsqrt_(dot(v1, v1)), i2 = rsqrt_(dot(v2, v2));
+  const V3<Real> e1 = i1 * v1, e2 = i2 * v2;
+  const Real cs = dot(e1, e2);
+  if (E) E[7] += c.K6 * ((Real)1 + cs);
+  f1 = (-c.K6 * i1) * (e2 - cs * e1);
+  f2 = (-c.K6 * i2) * (e1 - cs * e2);
+}
+
+// App. A Eq. 11, typed WCA; d = b_other - b_own, returns force on b_own.
+template <class Real>
+__device__ __forceinline__ V3<Real> t_wca(const Coef<Real>& c, V3<Real> d, Real s2sig, Real rc2, Real* e) {
+  const Real r2 = dot(d, d);
+  if (r2 >= rc2) { *e = (Real)0; return V3<Real>{0, 0, 0}; }
+  const Real s2 = s2sig / r2, s6 = s2 * s2 * s2;
+  *e = (Real)4 * c.eps * (s6 * s6 - s6 + (Real)0.25);
+  return ((Real)-24 * c.eps * s6 * ((Real)2 * s6 - (Real)1) / r2) * d;
+}
+
+template <class Real>
+__device__ __forceinline__ void vir_add(Real* W, V3<Real> r, V3<Real> f) {
+  W[0] += r.x * f.x; W[1] += r.y * f.y; W[2] += r.z * f.z;
+  W[3] += r.x * f.y; W[4] += r.x * f.z; W[5] += r.y * f.z;
+}
+
+// ---------------------------------------------------------------- grid barrier
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch that also ORs every block's flag
+// word.  The wait is bounded by a clock budget; on expiry the block reports
+// B_ETIMEOUT and the caller leaves the kernel.
+__device__ __forceinline__ unsigned grid_sync(GridBar* bar, unsigned nblocks,
+                                              unsigned local, unsigned long long budget, unsigned* s_word) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = ld_acquire(&bar->gen);
+    atomicOr(&bar->acc[g % 3], local);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar->count, 1u);
+    unsigned res = 0;
+    if (arrived == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      atomicExch(&bar->acc[(g + 1) % 3], 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const unsigned long long t0 = clock64();
+      unsigned ns = 32;
+      while (ld_acquire(&bar->gen) == g) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        if ((unsigned long long)(clock64() - t0) > budget) { res = B_ETIMEOUT; break; }
+      }
+    }
+    __threadfence();
+    res |= atomicOr(&bar->acc[g % 3], 0u);
+    *s_word = res;
+  }
+  __syncthreads();
+  return *s_word;
+}
+
+}  // namespace dsdna

@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA engine (through the C ABI) against the FP64 oracle.
+
+Tolerances (derived in DESIGN.md, "Parity tolerances"):
+  * FP64 engine forces: 1e-9 of the per-site force scale.
+  * Mixed engine (FP32 forces): 1e-5 of the per-site scale max(|F_i|, F_rms),
+    F_rms the RMS site force of the configuration.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1608_03722_gb300 import dsdna as D
+from paper_1608_03722_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [D.PREC_MIXED, D.PREC_FP64]
+TOL = {D.PREC_MIXED: 1e-5, D.PREC_FP64: 1e-9}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.init()
+    yield
+
+
+def oparams(cfg, **kw):
+    return O.params(box=cfg.box, **kw) if cfg.box[0] > 0 else O.params(**kw)
+
+
+def ctx_for(cfg, prec, X=None, u=None, **kw):
+    p = D.dsdna_default_params(precision=prec, box=cfg.box, **kw)
+    return D.Context(p, cfg.n_bp, X=cfg.X if X is None else X, V=cfg.V, u=cfg.u if u is None else u, Om=cfg.Om,
+                     tether=cfg.tether)
+
+
+def site_err(Fg, Fo):
+    scale = np.maximum(np.linalg.norm(Fo, axis=1), np.sqrt((Fo ** 2).sum(1).mean()))
+    return (np.linalg.norm(Fg - Fo, axis=1) / scale).max()
+
+
+def check_forces(cfg, prec, X=None, u=None, ext=False):
+    X = cfg.X if X is None else X
+    u = cfg.u if u is None else u
+    ctx = ctx_for(cfg, prec, X=X, u=u)
+    if ext:
+        for m in range(len(cfg.n_bp)):
+            ctx.set_external_force_torque(m, cfg.ext_f[m], cfg.ext_t[m])
+    Fb, Fp = ctx.compute_forces()
+    r = O.forces(oparams(cfg), cfg.n_bp, X, u, ext_f=cfg.ext_f if ext else None, ext_t=cfg.ext_t if ext else None)
+    eb, ep = site_err(Fb, r["Fb"]), site_err(Fp, r["Fp"])
+    ctx.close()
+    assert eb < TOL[prec] and ep < TOL[prec], (eb, ep)
+    return eb, ep
+
+
+def dense_walk(n_bp=3000, seed=1):
+    """Compressed self-avoiding helix in a small periodic box: many WCA contacts across images."""
+    cfg = I.c3_confined(n_bp=n_bp, phi=0.25, clearance=1.7, seed=seed)
+    rng = np.random.default_rng(seed)
+    cfg.X, cfg.u = I.perturb(cfg.X, cfg.u, rng, dx=0.01, dtheta=0.02)
+    return cfg
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_forces_ideal_helix(prec):
+    check_forces(I.c1_linear(200), prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n_bp", [1, 2, 3, 127, 128, 129, 200, 515])
+def test_forces_perturbed_lengths(prec, n_bp):
+    """Lengths around the 128-bp segment of a 256-thread CTA, plus the degenerate 1-3 bp molecules."""
+    cfg = I.c1_linear(n_bp)
+    rng = np.random.default_rng(n_bp)
+    X, u = I.perturb(cfg.X, cfg.u, rng, dx=0.03, dtheta=0.08)
+    check_forces(cfg, prec, X, u)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_forces_ragged_batch(prec):
+    cfg = I.ragged_batch([1, 5, 130, 64, 257, 2, 33], seed=3, spread=0.03)
+    check_forces(cfg, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_forces_periodic_dense(prec):
+    cfg = dense_walk()
+    r = O.forces(oparams(cfg), cfg.n_bp, cfg.X, cfg.u)
+    assert r["energy"][0, 3] > 1.0, "configuration must exercise the pair forces"
+    check_forces(cfg, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_forces_with_applied_load(prec):
+    cfg = I.c4_batch(n_mol=5, lo=20, hi=300, seed=2)
+    rng = np.random.default_rng(4)
+    cfg.X, cfg.u = I.perturb(cfg.X, cfg.u, rng, dx=0.02, dtheta=0.05)
+    check_forces(cfg, prec, ext=True)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_neighbor_pairs_equal_brute_force(prec):
+    cfg = dense_walk(1500, seed=5)
+    ctx = ctx_for(cfg, prec)
+    got = {tuple(x) for x in ctx.neighbor_pairs()}
+    skin = ctx.params.skin + 0.01   # the list radius carries a 0.01 margin over the skin
+    want = {tuple(x) for x in O.pairs(oparams(cfg), cfg.n_bp, cfg.X, cfg.u, extra=skin)}
+    # pairs within 1e-4 of the list radius may fall either way in FP32
+    lo = {tuple(x) for x in O.pairs(oparams(cfg), cfg.n_bp, cfg.X, cfg.u, extra=skin - 1e-4)}
+    hi = {tuple(x) for x in O.pairs(oparams(cfg), cfg.n_bp, cfg.X, cfg.u, extra=skin + 1e-4)}
+    assert lo <= got <= hi
+    assert len(want) > 1000
+    ctx.close()
+
+
+def test_fp64_trajectory_matches_oracle():
+    """Same seed, same uniform Philox noise: FP64 engine and oracle agree to round-off over 200 steps."""
+    cfg = I.c1_linear(200)
+    p = O.params(seed=11)
+    ctx = ctx_for(cfg, D.PREC_FP64, seed=11)
+    X, V, u, Om = (a.copy() for a in (cfg.X, cfg.V, cfg.u, cfg.Om))
+    O.run(p, cfg.n_bp, X, V, u, Om, 200)
+    ctx.step(200)
+    Xg, Vg, ug, Og = ctx.get_state()
+    assert np.abs(Xg - X).max() < 1e-9
+    assert np.abs(Vg - V).max() < 1e-7
+    assert np.abs(ug - u).max() < 1e-9
+    ctx.close()
+
+
+def test_mixed_trajectory_tracks_oracle():
+    """FP32 forces with FP64 accumulation stay on the oracle trajectory before chaotic divergence."""
+    cfg = I.c1_linear(200)
+    p = O.params(seed=12)
+    ctx = ctx_for(cfg, D.PREC_MIXED, seed=12)
+    X, V, u, Om = (a.copy() for a in (cfg.X, cfg.V, cfg.u, cfg.Om))
+    errs = []
+    for chunk in range(5):
+        O.run(p, cfg.n_bp, X, V, u, Om, 20, step0=20 * chunk)
+        ctx.step(20)
+        Xg, Vg, ug, Og = ctx.get_state()
+        errs.append(np.abs(Xg - X).max())
+    assert errs[-1] < 1e-4, errs
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_energy_and_virial_match_oracle(prec):
+    cfg = dense_walk(800, seed=7)
+    ctx = ctx_for(cfg, prec)
+    E, W = ctx.energy_virial()
+    Eo, Wo = O.energy(oparams(cfg), cfg.n_bp, cfg.X, cfg.V, cfg.u, cfg.Om, 0)
+    tol = 1e-9 if prec == D.PREC_FP64 else 2e-5
+    scale = np.abs(Eo[0]).sum()
+    assert np.abs(E - Eo[0]).max() < tol * scale, (E, Eo[0])
+    assert np.abs(W - Wo[0]).max() < tol * np.abs(Wo[0]).sum() * 10
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_observables_match_oracle(prec):
+    cfg = I.c1_linear(150)
+    rng = np.random.default_rng(9)
+    X, u = I.perturb(cfg.X, cfg.u, rng, dx=0.03, dtheta=0.05)
+    X[1::2][:10, 0] += 0.5      # break ten hydrogen bonds
+    ctx = ctx_for(cfg, prec, X=X, u=u)
+    o = ctx.observables(0, D.OBS_EXT | D.OBS_DENAT | D.OBS_TW | D.OBS_LK)
+    oo = O.observables(O.params(), cfg.n_bp, X, u, with_lk=True)
+    un = u / np.linalg.norm(u, axis=1, keepdims=True)
+    uf = np.ascontiguousarray(un.astype(np.float32).astype(np.float64))   # the engine keeps u in FP32
+    oo2 = O.observables(O.params(), cfg.n_bp, X, uf, with_lk=True)
+    for k in ("rz", "denat", "tw", "lk", "wr"):
+        ref = oo if prec == D.PREC_FP64 else oo2
+        assert abs(o[k] - ref[k]) < 1e-6 * max(1.0, abs(ref[k])), (k, o[k], ref[k])
+    assert o["denat"] == 10 / 150
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_checkpoint_resume_is_bitwise(prec):
+    """get_state at step 70 into a fresh context whose counter also stands at 70
+    continues bit for bit like the uninterrupted run (counter-based noise)."""
+    cfg = I.c1_linear(300)
+    a = ctx_for(cfg, prec, seed=3)
+    a.step(120)
+    ref = a.get_state()
+    b = ctx_for(cfg, prec, seed=3)
+    b.step(70)
+    s = b.get_state()
+    c = ctx_for(cfg, prec, seed=3)
+    c.step(70)
+    c.set_state(-1, *s)
+    c.step(50)
+    got = c.get_state()
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    for h in (a, b, c):
+        h.close()
+
+
+def test_broken_backbone_reports_efene_and_poisons():
+    cfg = I.c1_linear(40)
+    X = cfg.X.copy()
+    X[2 * 20:, 2] += 0.5          # stretch one backbone bond past R0
+    ctx = ctx_for(cfg, D.PREC_MIXED, X=X)
+    with pytest.raises(D.DsdnaError) as e:
+        ctx.compute_forces()
+    assert e.value.status == "EFENE"
+    with pytest.raises(D.DsdnaError) as e2:
+        ctx.step(1)
+    assert e2.value.status == "ESTATE"
+    ctx.set_state(-1, X=cfg.X, u=cfg.u)
+    Fb, Fp = ctx.compute_forces()
+    assert np.isfinite(Fb).all()
+    ctx.close()
+
+
+def test_neighbor_overflow_is_reported():
+    cfg = dense_walk(600, seed=8)
+    ctx = ctx_for(cfg, D.PREC_MIXED, max_neighbors=1)
+    with pytest.raises(D.DsdnaError) as e:
+        ctx.compute_forces()
+    assert e.value.status == "EOVERFLOW"
+    ctx.close()
+
+
+def test_invalid_arguments_are_rejected():
+    p = D.dsdna_default_params(block_threads=100)
+    with pytest.raises(D.DsdnaError) as e:
+        D.Context(p, [10])
+    assert e.value.status == "EINVAL"
+    p = D.dsdna_default_params(box=(10.0, 0.0, 10.0))
+    with pytest.raises(D.DsdnaError):
+        D.Context(p, [10])
+    ctx = D.Context(D.dsdna_default_params(), [10])
+    with pytest.raises(D.DsdnaError):
+        ctx.set_external_force_torque(3, [0, 0, 1], [0, 0, 0])
+    with pytest.raises(D.DsdnaError):
+        ctx.step(-1)
+    ctx.close()
+
+
+def test_library_builds_default_helix_like_oracle():
+    p = O.params(seed=21)
+    ctx = D.Context(D.dsdna_default_params(seed=21, precision=D.PREC_FP64), [64, 9], tether=[1, 0])
+    X, V, u, Om = ctx.get_state()
+    Xo, uo = O.ideal_helix(p, 64)
+    Vo, Omo = O.mb_velocities(p, 0, 64, uo, tether=1)
+    assert np.allclose(X[:128], Xo, atol=1e-12) and np.allclose(u[:128], uo, atol=1e-12)
+    assert np.allclose(V[:128], Vo, atol=1e-12) and np.allclose(Om[:128], Omo, atol=1e-12)
+    Vo1, Omo1 = O.mb_velocities(p, 1, 9, O.ideal_helix(p, 9)[1])
+    assert np.allclose(V[128:], Vo1, atol=1e-12)
+    ctx.close()
+
+
+def test_c3_full_size_sampled_forces():
+    """The 1 Mbp confined helix (2e6 nucleotides) of the throughput benchmark, at its
+    launch configuration, on a sample of nucleotides the oracle evaluates one by one."""
+    cfg = I.c3_confined()
+    ctx = ctx_for(cfg, D.PREC_MIXED)
+    Fb, Fp = ctx.compute_forces()
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(cfg.n_nt, size=300, replace=False))
+    ob, op = O.forces_sampled(oparams(cfg), cfg.n_bp, cfg.X, cfg.u, idx)
+    allF = np.concatenate([Fb, Fp])
+    rms = np.sqrt((allF ** 2).sum(1).mean())
+    for G, R in ((Fb[idx], ob), (Fp[idx], op)):
+        scale = np.maximum(np.linalg.norm(R, axis=1), rms)
+        assert (np.linalg.norm(G - R, axis=1) / scale).max() < 1e-5
+    ctx.step(20)
+    ctx.synchronize()
+    assert ctx.info()["rebuilds"] >= 1
+    ctx.close()
