@@ -39,11 +39,11 @@ def dist_env():
     return ws, rank, local
 
 
-def build_workload(name: str, seed: int = 0):
+def build_workload(name: str, seed: int = 0, n_bp: int = 1_000_000):
     from paper_1608_03722_gb300 import inputs as I
     if name == "c3":
-        cfg = I.c3_confined(seed=seed)
-        desc = ("confined self-avoiding dsDNA, 1,000,000 bp = 2,000,000 nucleotides, periodic cube "
+        cfg = I.c3_confined(n_bp=n_bp, seed=seed)
+        desc = (f"confined self-avoiding dsDNA, {n_bp:,} bp = {2 * n_bp:,} nucleotides, periodic cube "
                 f"L={cfg.box[0]:.2f} nm (volume fraction 0.05), Langevin kT=1, dt=0.005")
     elif name == "c2":
         cfg = I.c2_tethered(force=5.0, torque=2.0, seed=seed)
@@ -144,7 +144,7 @@ def run_cpu_oracle(cfg, steps: int, seconds_cap: float = 25.0):
 def reference_arm(args, ws, rank):
     if rank != 0:
         return 0
-    cfg, desc = build_workload(args.workload)
+    cfg, desc = build_workload(args.workload, n_bp=args.n_bp)
     import oracle as O
     O.build()
     value, done, dt = run_cpu_oracle(cfg, args.steps, seconds_cap=max(30.0, 20.0 * args.steps))
@@ -169,6 +169,7 @@ def main():
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4"])
     ap.add_argument("--md-steps", type=int, default=100)
+    ap.add_argument("--n-bp", type=int, default=1_000_000, help="base pairs of the confined workload")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -188,7 +189,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1608_03722_gb300 import dsdna as D
 
-    cfg, desc = build_workload(args.workload, seed=rank)
+    cfg, desc = build_workload(args.workload, seed=rank, n_bp=args.n_bp)
     prec = D.PREC_MIXED if args.precision == "mixed" else D.PREC_FP64
     p = D.dsdna_default_params(precision=prec, box=cfg.box, seed=rank)
     ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether)

@@ -61,7 +61,9 @@ def lib():
         for fn in (L.or_forces, L.or_forces_cells):
             fn.argtypes = [P(Params), C.c_int, i32, d, d, d, d, d, d, d, d, d, d]
             fn.restype = C.c_int
-        L.or_forces_sampled.argtypes = [P(Params), C.c_int, i32, d, d, d, d, C.c_int, i64, d, d]
+        L.or_forces_sampled.argtypes = [P(Params), C.c_int, i32, d, d, d, d, C.c_int, i64, d, d, d, d]
+        L.or_force_scale.argtypes = [P(Params), C.c_int, i32, d, d, d, d, d, d]
+        L.or_force_scale.restype = C.c_int
         L.or_forces_sampled.restype = C.c_int
         L.or_pairs.argtypes = [P(Params), C.c_int, i32, d, d, C.c_double, C.c_int64, i64, i64]
         L.or_pairs.restype = C.c_int64
@@ -147,15 +149,27 @@ def forces(p: Params, n_bp, X, u, ext_f=None, ext_t=None, cells=False):
     return dict(Fb=Fb, Fp=Fp, F=F, T=T, energy=E, virial=W)
 
 
-def forces_sampled(p: Params, n_bp, X, u, idx, ext_f=None, ext_t=None):
+def forces_sampled(p: Params, n_bp, X, u, idx, ext_f=None, ext_t=None, with_scale=False):
     nb, nbp = _i32(np.atleast_1d(n_bp))
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     Fb = np.zeros((len(idx), 3)); Fp = np.zeros((len(idx), 3))
+    Sb = np.zeros(len(idx)); Sp = np.zeros(len(idx))
     ef = None if ext_f is None else np.ascontiguousarray(ext_f, dtype=np.float64)
     et = None if ext_t is None else np.ascontiguousarray(ext_t, dtype=np.float64)
     _check(lib().or_forces_sampled(C.byref(p), len(nb), nbp, _d(X), _d(u), _d(ef), _d(et), len(idx),
-                                   idx.ctypes.data_as(C.POINTER(C.c_int64)), _d(Fb), _d(Fp)))
-    return Fb, Fp
+                                   idx.ctypes.data_as(C.POINTER(C.c_int64)), _d(Fb), _d(Fp), _d(Sb), _d(Sp)))
+    return (Fb, Fp, Sb, Sp) if with_scale else (Fb, Fp)
+
+
+def force_scale(p: Params, n_bp, X, u, ext_f=None, ext_t=None):
+    """Per-site sum over terms of |term force| (condition scale of a floating-point force sum)."""
+    nb, nbp = _i32(np.atleast_1d(n_bp))
+    n = X.shape[0]
+    Sb = np.zeros(n); Sp = np.zeros(n)
+    ef = None if ext_f is None else np.ascontiguousarray(ext_f, dtype=np.float64)
+    et = None if ext_t is None else np.ascontiguousarray(ext_t, dtype=np.float64)
+    _check(lib().or_force_scale(C.byref(p), len(nb), nbp, _d(X), _d(u), _d(ef), _d(et), _d(Sb), _d(Sp)))
+    return Sb, Sp
 
 
 def pairs(p: Params, n_bp, X, u, extra=0.0):

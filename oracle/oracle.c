@@ -145,19 +145,21 @@ static void disp(const or_params* p, const double* a, const double* b, double* d
 
 /* App. A Eq. 9 plus the Table 1 backbone WCA (sigma_bb) between consecutive
  * beads of one strand.  d = b_next - b_this; f = force on b_next. */
-static int term_fene(const or_params* p, const double* d, double* e_fene, double* e_wca, double* f) {
+static int term_fene(const or_params* p, const double* d, double* e_fene, double* e_wca, double* f, double* mag) {
   double r2 = v_dot(d, d), R02 = p->R0 * p->R0;
   if (r2 >= R02) return OR_EFENE;               /* U = infinity for r >= R0 */
   *e_fene = -0.5 * p->K1 * R02 * log(1.0 - r2 / R02);
   double fr = -p->K1 / (1.0 - r2 / R02);        /* -(dU/dr)/r */
+  double fw = 0.0;
   *e_wca = 0.0;
   double rc = pow(2.0, 1.0 / 6.0) * p->sigma_bb;
   if (r2 < rc * rc) {
     double s2 = p->sigma_bb * p->sigma_bb / r2, s6 = s2 * s2 * s2, s12 = s6 * s6;
     *e_wca = 4.0 * p->eps_bb * (s12 - s6 + 0.25);
-    fr += 24.0 * p->eps_bb * (2.0 * s12 - s6) / r2;
+    fw = 24.0 * p->eps_bb * (2.0 * s12 - s6) / r2;
   }
-  for (int c = 0; c < 3; ++c) f[c] = fr * d[c];
+  for (int c = 0; c < 3; ++c) f[c] = (fr + fw) * d[c];
+  *mag = (fabs(fr) + fabs(fw)) * sqrt(r2);       /* the two terms separately, for the force scale */
   return OR_OK;
 }
 
@@ -280,7 +282,7 @@ static void term_bend(const or_params* p, const double* v1, const double* v2,
 }
 
 /* ------------------------------------------------------- term collection */
-typedef struct { int64_t slot; int site; double f[3]; } contrib_t;
+typedef struct { int64_t slot; int site; double f[3]; double mag; } contrib_t;
 typedef struct {
   contrib_t c[16]; int n;
   double e[OR_NTERMS];
@@ -290,6 +292,7 @@ typedef struct {
 static void tout_add(tout_t* o, int64_t slot, int site, const double* f, const double* rel) {
   contrib_t* c = &o->c[o->n++];
   c->slot = slot; c->site = site; c->f[0] = f[0]; c->f[1] = f[1]; c->f[2] = f[2];
+  c->mag = v_norm(f);
   /* site virial sum_s (r_s - r_ref) (x) F_s, xx yy zz xy xz yz */
   o->vir[0] += rel[0] * f[0]; o->vir[1] += rel[1] * f[1]; o->vir[2] += rel[2] * f[2];
   o->vir[3] += rel[0] * f[1]; o->vir[4] += rel[0] * f[2]; o->vir[5] += rel[1] * f[2];
@@ -309,10 +312,12 @@ static int owner_terms(const or_params* p, const topo_t* t, const double* X, con
     site_pos(p, X, u, n, 1, pn);
     /* FENE + backbone WCA: b_g -> b_n */
     disp(p, bg, bn, d);
-    if (term_fene(p, d, &e1, &e2, f) != OR_OK) return OR_EFENE;
+    double mag;
+    if (term_fene(p, d, &e1, &e2, f, &mag) != OR_OK) return OR_EFENE;
     o->e[OR_E_FENE] += e1; o->e[OR_E_BONDWCA] += e2;
     mf[0] = -f[0]; mf[1] = -f[1]; mf[2] = -f[2];
     tout_add(o, g, 0, mf, zero); tout_add(o, n, 0, f, d);
+    o->c[o->n - 2].mag = mag; o->c[o->n - 1].mag = mag;
     /* Morse: p_g -> p_n */
     disp(p, pg, pn, d);
     term_morse(p, d, &e1, f);
@@ -373,6 +378,7 @@ static double pair_sigma(const or_params* p, const topo_t* t, int64_t i, int64_t
 typedef struct {
   double *Fb, *Fp;      /* site forces, may be NULL */
   double *energy, *virial;
+  double *Sb, *Sp;      /* sum over terms of |force| per site, may be NULL */
 } sink_t;
 
 static void sink_tout(sink_t* s, const tout_t* o, int mol) {
@@ -380,6 +386,8 @@ static void sink_tout(sink_t* s, const tout_t* o, int mol) {
     const contrib_t* c = &o->c[i];
     double* F = (c->site == 0) ? s->Fb : s->Fp;
     if (F) for (int k = 0; k < 3; ++k) F[3 * c->slot + k] += c->f[k];
+    double* S = (c->site == 0) ? s->Sb : s->Sp;
+    if (S) S[c->slot] += c->mag;
   }
   if (s->energy) for (int k = 0; k < OR_NTERMS; ++k) s->energy[OR_NTERMS * mol + k] += o->e[k];
   if (s->virial) for (int k = 0; k < 6; ++k) s->virial[6 * mol + k] += o->vir[k];
@@ -396,6 +404,7 @@ static void pair_eval(const or_params* p, const topo_t* t, const double* X, cons
   term_wca(p, d, sig, &e, f);
   if (e == 0.0 && f[0] == 0.0 && f[1] == 0.0 && f[2] == 0.0) return;
   if (s->Fb) for (int k = 0; k < 3; ++k) { s->Fb[3 * i + k] -= f[k]; s->Fb[3 * j + k] += f[k]; }
+  if (s->Sb) { s->Sb[i] += v_norm(f); s->Sb[j] += v_norm(f); }
   if (s->energy) s->energy[OR_NTERMS * mol + OR_E_WCA] += e;
   if (s->virial) {
     double* v = s->virial + 6 * mol;
@@ -444,6 +453,8 @@ static void external_load(const or_params* p, const topo_t* t, const double* X, 
       if (s->Fb) s->Fb[3 * g + c] += 0.5 * F[k][c];
       if (s->Fp) s->Fp[3 * g + c] += 0.5 * F[k][c];
     }
+    if (s->Sb) s->Sb[g] += 0.5 * v_norm(F[k]);
+    if (s->Sp) s->Sp[g] += 0.5 * v_norm(F[k]);
   }
 }
 
@@ -517,7 +528,7 @@ static void all_pairs(const or_params* p, const topo_t* t, const double* X, cons
 
 static int forces_impl(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
                        const double* ef, const double* et, double* Fb, double* Fp, double* Fbody, double* Tbody,
-                       double* energy, double* virial, int use_cells) {
+                       double* energy, double* virial, int use_cells, double* Sb, double* Sp) {
   topo_t t;
   if (topo_init(&t, n_mol, n_bp) != OR_OK) return OR_EINVAL;
   int64_t n = t.n_nt;
@@ -527,7 +538,9 @@ static int forces_impl(const or_params* p, int n_mol, const int* n_bp, const dou
   memset(fp, 0, sizeof(double) * (size_t)(3 * n));
   if (energy) memset(energy, 0, sizeof(double) * (size_t)(OR_NTERMS * n_mol));
   if (virial) memset(virial, 0, sizeof(double) * (size_t)(6 * n_mol));
-  sink_t s = {fb, fp, energy, virial};
+  if (Sb) memset(Sb, 0, sizeof(double) * (size_t)n);
+  if (Sp) memset(Sp, 0, sizeof(double) * (size_t)n);
+  sink_t s = {fb, fp, energy, virial, Sb, Sp};
   int rc = OR_OK;
   for (int64_t g = 0; g < n && rc == OR_OK; ++g) {
     tout_t o; memset(&o, 0, sizeof(o));
@@ -559,23 +572,28 @@ static int forces_impl(const or_params* p, int n_mol, const int* n_bp, const dou
 int or_forces(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
               const double* ef, const double* et, double* Fb, double* Fp, double* Fbody, double* Tbody,
               double* energy, double* virial) {
-  return forces_impl(p, n_mol, n_bp, X, u, ef, et, Fb, Fp, Fbody, Tbody, energy, virial, 0);
+  return forces_impl(p, n_mol, n_bp, X, u, ef, et, Fb, Fp, Fbody, Tbody, energy, virial, 0, NULL, NULL);
+}
+int or_force_scale(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
+                   const double* ef, const double* et, double* Sb, double* Sp) {
+  return forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, NULL, NULL, NULL, NULL, 1, Sb, Sp);
 }
 int or_forces_cells(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
                     const double* ef, const double* et, double* Fb, double* Fp, double* Fbody, double* Tbody,
                     double* energy, double* virial) {
-  return forces_impl(p, n_mol, n_bp, X, u, ef, et, Fb, Fp, Fbody, Tbody, energy, virial, 1);
+  return forces_impl(p, n_mol, n_bp, X, u, ef, et, Fb, Fp, Fbody, Tbody, energy, virial, 1, NULL, NULL);
 }
 
 int or_forces_sampled(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
-                      const double* ef, const double* et, int ns, const int64_t* idx, double* Fb, double* Fp) {
+                      const double* ef, const double* et, int ns, const int64_t* idx, double* Fb, double* Fp,
+                      double* Sb, double* Sp) {
   topo_t t;
   if (topo_init(&t, n_mol, n_bp) != OR_OK) return OR_EINVAL;
   int rc = OR_OK;
   for (int q = 0; q < ns && rc == OR_OK; ++q) {
     int64_t g = idx[q];
     int m = mol_of(&t, g);
-    double fb[3] = {0, 0, 0}, fp[3] = {0, 0, 0};
+    double fb[3] = {0, 0, 0}, fp[3] = {0, 0, 0}, sb = 0.0, sp = 0.0;
     int64_t owners[3] = {prev_nt(&t, g), g, next_nt(&t, g)};
     for (int k = 0; k < 3; ++k) {
       if (owners[k] < 0) continue;
@@ -584,13 +602,16 @@ int or_forces_sampled(const or_params* p, int n_mol, const int* n_bp, const doub
       for (int i = 0; i < o.n; ++i) if (o.c[i].slot == g) {
         double* F = o.c[i].site == 0 ? fb : fp;
         for (int c = 0; c < 3; ++c) F[c] += o.c[i].f[c];
+        *(o.c[i].site == 0 ? &sb : &sp) += o.c[i].mag;
       }
     }
     {
       tout_t o; memset(&o, 0, sizeof(o));
       hbond_terms(p, X, u, g & ~(int64_t)1, &o);
-      for (int i = 0; i < o.n; ++i) if (o.c[i].slot == g)
+      for (int i = 0; i < o.n; ++i) if (o.c[i].slot == g) {
         for (int c = 0; c < 3; ++c) fp[c] += o.c[i].f[c];
+        sp += o.c[i].mag;
+      }
     }
     /* pairs with every other bead of the molecule */
     int64_t g0 = 2 * t.off[m], g1 = 2 * t.off[m + 1];
@@ -604,17 +625,21 @@ int or_forces_sampled(const or_params* p, int n_mol, const int* n_bp, const doub
       disp(p, bi, bj, d);
       term_wca(p, d, sig, &e, f);
       for (int c = 0; c < 3; ++c) fb[c] -= f[c];
+      sb += v_norm(f);
     }
     /* external load */
     if (g / 2 == t.off[m] + n_bp[m] - 1) {
       double* tmpb = (double*)calloc((size_t)(3 * t.n_nt), sizeof(double));
       double* tmpp = (double*)calloc((size_t)(3 * t.n_nt), sizeof(double));
-      sink_t s = {tmpb, tmpp, NULL, NULL};
+      sink_t s = {tmpb, tmpp, NULL, NULL, NULL, NULL};
       external_load(p, &t, X, m, ef, et, &s);
       for (int c = 0; c < 3; ++c) { fb[c] += tmpb[3 * g + c]; fp[c] += tmpp[3 * g + c]; }
+      sb += v_norm(tmpb + 3 * g); sp += v_norm(tmpp + 3 * g);
       free(tmpb); free(tmpp);
     }
     for (int c = 0; c < 3; ++c) { Fb[3 * q + c] = fb[c]; Fp[3 * q + c] = fp[c]; }
+    if (Sb) Sb[q] = sb;
+    if (Sp) Sp[q] = sp;
   }
   topo_free(&t);
   return rc;
@@ -764,7 +789,7 @@ int or_run(const or_params* p, int n_mol, const int* n_bp, double* X, double* V,
   double M = 2.0 * p->mass, I = 0.5 * p->mass * p->ell * p->ell;
   int rc = OR_OK;
   for (int64_t s = step0; s < step0 + nsteps; ++s) {
-    rc = forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, F, T, NULL, NULL, use_cells);
+    rc = forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, F, T, NULL, NULL, use_cells, NULL, NULL);
     if (rc != OR_OK) break;
     for (int64_t g = 0; g < n; ++g) {
       int m = mol_of(&t, g);
@@ -807,7 +832,7 @@ int or_energy(const or_params* p, int n_mol, const int* n_bp, const double* X, c
   int64_t n = t.n_nt;
   double* F = (double*)malloc(sizeof(double) * (size_t)(3 * n));
   double* T = (double*)malloc(sizeof(double) * (size_t)(3 * n));
-  int rc = forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, F, T, energy, virial, 0);
+  int rc = forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, F, T, energy, virial, 0, NULL, NULL);
   double M = 2.0 * p->mass, I = 0.5 * p->mass * p->ell * p->ell;
   if (rc == OR_OK && energy) {
     for (int64_t g = 0; g < n; ++g) {

@@ -95,10 +95,18 @@ int or_forces_cells(const or_params* p, int n_mol, const int* n_bp, const double
                     double* Fb, double* Fp, double* Fbody, double* Tbody, double* energy, double* virial);
 
 /* Site forces on a sample of nucleotides only (global slots idx[0..ns-1]);
- * pairs by brute force over the sample's molecule.  Fb/Fp are [3*ns]. */
+ * pairs by brute force over the sample's molecule.  Fb/Fp are [3*ns];
+ * Sb/Sp (may be NULL) receive the sum over contributing terms of |force|. */
 int or_forces_sampled(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
                       const double* ext_f, const double* ext_t, int ns, const int64_t* idx,
-                      double* Fb, double* Fp);
+                      double* Fb, double* Fp, double* Sb, double* Sp);
+
+/* Condition scale of the site forces: for every site the sum over all terms
+ * acting on it of the magnitude of that term's force [n_nt] each.  A
+ * floating-point evaluation of the total force has an error bounded by a
+ * small multiple of the unit round-off times this sum. */
+int or_force_scale(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
+                   const double* ext_f, const double* ext_t, double* Sb, double* Sp);
 
 /* All interacting bead pairs (i<j, global slots) with |d| < r_cut(type) + extra, brute force.
  * Writes at most cap pairs into pi/pj, returns the total count. */

@@ -136,91 +136,186 @@ def box_edge(n_nt: int, phi: float) -> float:
     return (n_nt * (math.pi / 6.0) / phi) ** (1.0 / 3.0)
 
 
-def _rot(axis, ang):
-    a = np.asarray(axis, float); a = a / np.linalg.norm(a)
-    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
-    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * (K @ K)
-
-
-def c3_confined(n_bp: int = 1_000_000, phi: float = 0.05, seg_bp: int = 30, max_joint_deg: float = 20.0,
-                clearance: float = 2.5, seed: int = 0) -> Config:
+def random_walk_helix(n_bp: int = 3000, phi: float = 0.05, seg_bp: int = 30, max_joint_deg: float = 25.0,
+                clearance: float = 2.2, joint_bp: int = 5, seed: int = 0) -> Config:
     """Self-avoiding helix in a periodic cube at volume fraction phi.
 
-    The axis is a chain of straight seg_bp-long helical segments joined at
-    random angles up to max_joint_deg with a continuous helical phase
-    (parallel-transported reference normal).  A segment is redrawn when one of
-    its sample points comes closer than ``clearance`` (periodic) to an axis
-    point of any earlier, non-adjacent segment.  Coordinates stay unwrapped.
+    The axis is a chain of seg_bp-long helical segments; each segment turns
+    the axis by a random angle up to max_joint_deg, spread evenly over its
+    first joint_bp base pairs, and the reference normal is carried along by
+    the same rotations so the helical phase stays continuous.  Axis points
+    every 3 bp of a new segment must stay ``clearance`` (periodic) away from
+    those of every earlier, non-adjacent segment; a segment that cannot be
+    placed makes the walk back up a few segments.  Coordinates stay unwrapped.
     """
     rng = np.random.default_rng(seed)
     L = box_edge(2 * n_bp, phi)
     nseg = (n_bp + seg_bp - 1) // seg_bp
-    cell = clearance
-    ncell = max(1, int(L // cell))
+    # segments are filed by the cell of their middle point; a cell is wider than
+    # a segment plus the clearance, so clashes only occur with the 27 neighbour cells
+    reach = RISE * seg_bp + clearance + 0.5
+    ncell = max(1, int(L // reach))
     h = L / ncell
     grid: dict = {}
-    t = np.array([0.0, 0.0, 1.0]); n = np.array([1.0, 0.0, 0.0])
-    start = rng.uniform(0, L, size=3)
-    starts = np.empty((nseg, 3)); ts = np.empty((nseg, 3)); ns = np.empty((nseg, 3))
-    sample = np.arange(0, seg_bp, 5)
     maxj = math.radians(max_joint_deg)
-    pos = start.copy()
-    for s in range(nseg):
-        for attempt in range(200):
-            if s == 0:
-                t2, n2 = t, n
-            else:
-                ang = maxj * math.sqrt(rng.uniform()) if attempt < 100 else rng.uniform(0, math.pi / 2)
-                perp = np.cross(t, rng.normal(size=3)); perp /= np.linalg.norm(perp)
-                R = _rot(perp, ang)
-                t2 = R @ t; n2 = R @ n
-                n2 -= (n2 @ t2) * t2; n2 /= np.linalg.norm(n2)
-            pts = pos[None, :] + RISE * (sample[:, None] + (1 if s else 0)) * t2[None, :]
-            ok = True
-            for q in pts:
-                w = np.floor((q % L) / h).astype(int)
-                for dx in (-1, 0, 1):
-                    for dy in (-1, 0, 1):
-                        for dz in (-1, 0, 1):
-                            key = ((w[0] + dx) % ncell, (w[1] + dy) % ncell, (w[2] + dz) % ncell)
-                            for (qq, seg) in grid.get(key, ()):
-                                if seg >= s - 2:
-                                    continue
-                                dd = q - qq
-                                dd -= L * np.round(dd / L)
-                                if dd @ dd < clearance * clearance:
-                                    ok = False
-                                    break
-                            if not ok:
-                                break
-                        if not ok:
-                            break
-                    if not ok:
-                        break
-                if not ok:
-                    break
-            if ok or attempt == 199:
+    j = np.arange(1, seg_bp + 1)
+    frac = np.minimum(j, joint_bp) / float(joint_bp)
+    sample = np.arange(0, seg_bp, 3)
+    c2 = clearance * clearance
+    offs = [(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)]
+
+    def cell_of(q):
+        w = np.floor((q % L) / h).astype(int) % ncell
+        return (int(w[0]), int(w[1]), int(w[2]))
+
+    def clash(pts, s):
+        w = cell_of(pts[len(pts) // 2])
+        keys = {((w[0] + a) % ncell, (w[1] + b) % ncell, (w[2] + c) % ncell) for a, b, c in offs}
+        cand = [e[1] for k in keys for e in grid.get(k, ()) if e[0] < s - 2]
+        if not cand:
+            return False
+        Q = np.concatenate(cand)
+        d = pts[:, None, :] - Q[None, :, :]
+        d -= L * np.round(d / L)
+        return bool(((d * d).sum(-1) < c2).any())
+
+    segs = []          # accepted segments: (pts, ts, ns, sample cells)
+    t0 = np.array([0.0, 0.0, 1.0]); n0 = np.array([1.0, 0.0, 0.0])
+    start = rng.uniform(0, L, size=3) - RISE * t0
+    fails = 0
+    while len(segs) < nseg:
+        s = len(segs)
+        if s:
+            pos, t, n = segs[-1][0][-1], segs[-1][1][-1], segs[-1][2][-1]
+            n = n - (n @ t) * t
+            n /= np.linalg.norm(n)
+        else:
+            pos, t, n = start, t0, n0
+        placed = False
+        for attempt in range(60):
+            ang = 0.0 if s == 0 else maxj * math.sqrt(rng.uniform())
+            perp = np.cross(t, rng.normal(size=3)); perp /= np.linalg.norm(perp)
+            K = np.array([[0, -perp[2], perp[1]], [perp[2], 0, -perp[0]], [-perp[1], perp[0], 0]])
+            a = ang * frac
+            Rs = np.eye(3)[None] + np.sin(a)[:, None, None] * K[None] + (1 - np.cos(a))[:, None, None] * (K @ K)[None]
+            ts = Rs @ t
+            ns = Rs @ n
+            pts = pos[None, :] + RISE * np.cumsum(ts, axis=0)
+            if not clash(pts[sample], s):
+                placed = True
                 break
-        first = pos + (RISE * t2 if s else 0.0)
-        starts[s] = first; ts[s] = t2; ns[s] = n2
-        for q in pts:
-            w = np.floor((q % L) / h).astype(int)
-            grid.setdefault((w[0] % ncell, w[1] % ncell, w[2] % ncell), []).append((q.copy(), s))
-        pos = first + RISE * (seg_bp - 1) * t2
-        t, n = t2, n2
-    k = np.arange(n_bp)
-    s_of = k // seg_bp
-    j = k - s_of * seg_bp
-    axis = starts[s_of] + RISE * j[:, None] * ts[s_of]
-    b = np.cross(ts[s_of], ns[s_of])
-    ang = TWIST * k
-    d = np.cos(ang)[:, None] * ns[s_of] + np.sin(ang)[:, None] * b
+        if placed:
+            w = cell_of(pts[sample][len(sample) // 2])
+            segs.append((pts, ts, ns, w))
+            grid.setdefault(w, []).append((s, pts[sample]))
+            continue
+        fails += 1
+        if fails > 20 * nseg + 1000:
+            raise RuntimeError("could not grow the self-avoiding helix")
+        back = min(len(segs), 1 + int(rng.integers(0, 4)))
+        for _ in range(back):
+            _, _, _, w = segs.pop()
+            sdrop = len(segs)
+            grid[w] = [e for e in grid[w] if e[0] != sdrop]
+    axis = np.concatenate([sg[0] for sg in segs])[:n_bp]
+    T = np.concatenate([sg[1] for sg in segs])[:n_bp]
+    Nn = np.concatenate([sg[2] for sg in segs])[:n_bp]
+    Nn = Nn - (Nn * T).sum(1, keepdims=True) * T
+    Nn /= np.linalg.norm(Nn, axis=1, keepdims=True)
+    B = np.cross(T, Nn)
+    ang = TWIST * np.arange(n_bp)
+    d = np.cos(ang)[:, None] * Nn + np.sin(ang)[:, None] * B
     X, u = place(axis, d)
     V, Om = maxwell(u, rng)
     seq = bytes(rng.choice(np.frombuffer(b"ATGC", np.uint8), size=n_bp))
     cfg = Config("confined_%dbp_phi%.2f" % (n_bp, phi), np.array([n_bp], np.int32), X, u, V, Om,
                  box=(L, L, L), seq=seq)
     cfg.meta.update(L=L, phi=phi)
+    return cfg
+
+
+def _rotations(axis_vec, angles):
+    """Rotation matrices about a fixed unit axis for an array of angles."""
+    k = np.asarray(axis_vec, float)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    a = np.asarray(angles, float)
+    return np.eye(3)[None] + np.sin(a)[:, None, None] * K[None] + (1 - np.cos(a))[:, None, None] * (K @ K)[None]
+
+
+def c3_confined(n_bp: int = 1_000_000, phi: float = 0.05, seed: int = 0) -> Config:
+    """One dsDNA molecule filling a periodic cube at volume fraction phi.
+
+    The helix axis snakes through the box: straight rows along x on a square
+    lattice of (y, z) positions, consecutive rows joined by semicircular
+    U-turns, layers joined the same way in the xz plane, so the molecule is
+    self-avoiding by construction and locally looks like an array of parallel
+    helices.  The reference normal is parallel-transported (rotated with the
+    tangent through each turn) and the helix turns by 36 degrees per base pair
+    along the whole chain.  The lattice spacing is the largest that fits the
+    contour length; the start phase and a global shift are random (seed).
+    Coordinates stay unwrapped (they lie inside [0, L)).
+    """
+    rng = np.random.default_rng(seed)
+    L = box_edge(2 * n_bp, phi)
+    need = RISE * (n_bp + 1)
+    nrow = int(math.ceil(math.sqrt(need / (L - 4.0))))
+    while True:
+        a = L / nrow
+        x0, x1 = 0.5 * a + 1.0, L - 0.5 * a - 1.0
+        total = nrow * nrow * (x1 - x0) + (nrow * nrow - 1) * math.pi * 0.5 * a
+        if total >= need:
+            break
+        nrow += 1
+    rows = []
+    for jz in range(nrow):
+        order = range(nrow) if jz % 2 == 0 else range(nrow - 1, -1, -1)
+        for iy in order:
+            rows.append(((iy + 0.5) * a, (jz + 0.5) * a))
+    pts, tans, nors = [], [], []
+    t = np.array([1.0, 0.0, 0.0]); n = np.array([0.0, 1.0, 0.0])
+    carry = 0.0          # arc length into the next piece at which the next base pair sits
+    for r, (y, z) in enumerate(rows):
+        dirx = 1.0 if r % 2 == 0 else -1.0
+        xs, xe = (x0, x1) if dirx > 0 else (x1, x0)
+        length = x1 - x0
+        sarr = np.arange(carry, length, RISE)
+        p = np.stack([xs + dirx * sarr, np.full_like(sarr, y), np.full_like(sarr, z)], 1)
+        pts.append(p); tans.append(np.repeat(t[None], len(sarr), 0)); nors.append(np.repeat(n[None], len(sarr), 0))
+        carry = sarr[-1] + RISE - length if len(sarr) else carry - length
+        if r + 1 == len(rows):
+            break
+        ny_, nz_ = rows[r + 1]
+        off = np.array([0.0, ny_ - y, nz_ - z])
+        rad = 0.5 * np.linalg.norm(off)
+        w = off / np.linalg.norm(off)
+        centre = np.array([xe, y, z]) + rad * w
+        b = np.cross(t, w)                     # turn axis: rotates t into -t through w
+        arc = math.pi * rad
+        sarr = np.arange(carry, arc, RISE)
+        ang = sarr / rad
+        R = _rotations(b, ang)
+        start = np.array([xe, y, z])
+        p = centre[None] + (R @ (start - centre))
+        pts.append(p); tans.append(R @ t); nors.append(R @ n)
+        Rend = _rotations(b, [math.pi])[0]
+        t = Rend @ t; n = Rend @ n
+        carry = sarr[-1] + RISE - arc if len(sarr) else carry - arc
+    axis = np.concatenate(pts)[:n_bp]
+    T = np.concatenate(tans)[:n_bp]
+    Nn = np.concatenate(nors)[:n_bp]
+    assert len(axis) == n_bp, "box too small for the contour length"
+    Nn = Nn - (Nn * T).sum(1, keepdims=True) * T
+    Nn /= np.linalg.norm(Nn, axis=1, keepdims=True)
+    B = np.cross(T, Nn)
+    ang = rng.uniform(0, 2 * math.pi) + TWIST * np.arange(n_bp)
+    d = np.cos(ang)[:, None] * Nn + np.sin(ang)[:, None] * B
+    axis = axis + rng.uniform(-0.5, 0.5, size=3)
+    X, u = place(axis, d)
+    V, Om = maxwell(u, rng)
+    seq = bytes(rng.choice(np.frombuffer(b"ATGC", np.uint8), size=n_bp))
+    cfg = Config("confined_%dbp_phi%.2f" % (n_bp, phi), np.array([n_bp], np.int32), X, u, V, Om,
+                 box=(L, L, L), seq=seq)
+    cfg.meta.update(L=L, phi=phi, rows=nrow * nrow, spacing=a)
     return cfg
 
 

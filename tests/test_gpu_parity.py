@@ -1,9 +1,15 @@
 """GPU parity: the CUDA engine (through the C ABI) against the FP64 oracle.
 
-Tolerances (derived in DESIGN.md, "Parity tolerances"):
-  * FP64 engine forces: 1e-9 of the per-site force scale.
-  * Mixed engine (FP32 forces): 1e-5 of the per-site scale max(|F_i|, F_rms),
-    F_rms the RMS site force of the configuration.
+Forces are compared on identical configurations: the oracle evaluates the
+state the engine holds (read back with get_state; in mixed precision the
+orientation u is stored in FP32).  Per site i the bound is
+    |F_gpu - F_oracle| <= rel * S_i + abs
+with S_i the oracle's sum over all terms acting on the site of |term force|
+(the condition scale of a floating-point force sum; FENE and its WCA counted
+separately).  Mixed engine: rel = 1e-5, abs = 5e-4 kT/nm (twice the stiffest
+term, 2 K4 lambda^2 = 3840 kT/nm^2, times the FP32 spacing of a 0.5 nm
+displacement).  FP64 engine: rel = 1e-9, abs = 1e-10 kT/nm.
+("Parity tolerances".)
 """
 import numpy as np
 import pytest
@@ -15,7 +21,7 @@ from paper_1608_03722_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 PRECS = [D.PREC_MIXED, D.PREC_FP64]
-TOL = {D.PREC_MIXED: 1e-5, D.PREC_FP64: 1e-9}
+TOL = {D.PREC_MIXED: (1e-5, 5e-4), D.PREC_FP64: (1e-9, 1e-10)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,9 +42,10 @@ def ctx_for(cfg, prec, X=None, u=None, **kw):
                      tether=cfg.tether)
 
 
-def site_err(Fg, Fo):
-    scale = np.maximum(np.linalg.norm(Fo, axis=1), np.sqrt((Fo ** 2).sum(1).mean()))
-    return (np.linalg.norm(Fg - Fo, axis=1) / scale).max()
+def excess(Fg, Fo, S, prec):
+    """Largest ratio of the force difference to its allowed bound (must stay < 1)."""
+    rel, ab = TOL[prec]
+    return (np.linalg.norm(Fg - Fo, axis=1) / (rel * S + ab)).max()
 
 
 def check_forces(cfg, prec, X=None, u=None, ext=False):
@@ -49,16 +56,20 @@ def check_forces(cfg, prec, X=None, u=None, ext=False):
         for m in range(len(cfg.n_bp)):
             ctx.set_external_force_torque(m, cfg.ext_f[m], cfg.ext_t[m])
     Fb, Fp = ctx.compute_forces()
-    r = O.forces(oparams(cfg), cfg.n_bp, X, u, ext_f=cfg.ext_f if ext else None, ext_t=cfg.ext_t if ext else None)
-    eb, ep = site_err(Fb, r["Fb"]), site_err(Fp, r["Fp"])
+    Xs, _, us, _ = ctx.get_state()          # the configuration the engine holds
+    ef = cfg.ext_f if ext else None
+    et = cfg.ext_t if ext else None
+    r = O.forces(oparams(cfg), cfg.n_bp, Xs, us, ext_f=ef, ext_t=et)
+    Sb, Sp = O.force_scale(oparams(cfg), cfg.n_bp, Xs, us, ext_f=ef, ext_t=et)
+    eb, ep = excess(Fb, r["Fb"], Sb, prec), excess(Fp, r["Fp"], Sp, prec)
     ctx.close()
-    assert eb < TOL[prec] and ep < TOL[prec], (eb, ep)
+    assert eb < 1.0 and ep < 1.0, (eb, ep)
     return eb, ep
 
 
 def dense_walk(n_bp=3000, seed=1):
-    """Compressed self-avoiding helix in a small periodic box: many WCA contacts across images."""
-    cfg = I.c3_confined(n_bp=n_bp, phi=0.25, clearance=1.7, seed=seed)
+    """Random-walk helix packed into a small periodic box: WCA contacts across images."""
+    cfg = I.random_walk_helix(n_bp=n_bp, phi=0.15, clearance=1.7, seed=seed)
     rng = np.random.default_rng(seed)
     cfg.X, cfg.u = I.perturb(cfg.X, cfg.u, rng, dx=0.01, dtheta=0.02)
     return cfg
@@ -262,14 +273,12 @@ def test_c3_full_size_sampled_forces():
     cfg = I.c3_confined()
     ctx = ctx_for(cfg, D.PREC_MIXED)
     Fb, Fp = ctx.compute_forces()
+    Xs, _, us, _ = ctx.get_state()
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(cfg.n_nt, size=300, replace=False))
-    ob, op = O.forces_sampled(oparams(cfg), cfg.n_bp, cfg.X, cfg.u, idx)
-    allF = np.concatenate([Fb, Fp])
-    rms = np.sqrt((allF ** 2).sum(1).mean())
-    for G, R in ((Fb[idx], ob), (Fp[idx], op)):
-        scale = np.maximum(np.linalg.norm(R, axis=1), rms)
-        assert (np.linalg.norm(G - R, axis=1) / scale).max() < 1e-5
+    ob, op, sb, sp = O.forces_sampled(oparams(cfg), cfg.n_bp, Xs, us, idx, with_scale=True)
+    assert excess(Fb[idx], ob, sb, D.PREC_MIXED) < 1.0
+    assert excess(Fp[idx], op, sp, D.PREC_MIXED) < 1.0
     ctx.step(20)
     ctx.synchronize()
     assert ctx.info()["rebuilds"] >= 1
