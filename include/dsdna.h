@@ -222,6 +222,37 @@ const char* dsdna_last_error(const dsdna_ctx* ctx);
 /* Release every device buffer and the context. */
 void dsdna_destroy(dsdna_ctx* ctx);
 
+/* Force pass that allocates nothing.  The paper has no counterpart: this call
+ * exists for callers that cannot call cudaMalloc, such as processes whose
+ * device memory is wholly owned by another pool allocator, or tight loops
+ * that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * It computes the same conservative site forces as dsdna_compute_forces
+ * (mixed precision, no applied loads, nothing anchored) for the molecules
+ * n_bp[0..n_mol-1] at centres X and orientations u, without a context.
+ * X, u (inputs) and F_bead, F_patch (outputs) are caller-owned DEVICE arrays
+ * of 3*n_nt doubles in the AoS slot layout described above; n_bp is a host
+ * array.  Work runs on cuda_stream and the call waits for it.
+ *
+ * Limits: at most DSDNA_NOALLOC_MAX_NT nucleotides and DSDNA_NOALLOC_MAX_MOL
+ * molecules; a periodic box may span at most 32 cells of edge
+ * 2^(1/6) max(sigma) + skin per direction; precision must be
+ * DSDNA_PREC_MIXED.  Larger inputs return DSDNA_EINVAL.
+ *
+ * Scratch memory: one fixed device array of about 5 MB (cell table,
+ * neighbour list, position mirrors), reserved on every GPU that loads the
+ * library until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture.  Every call reuses the same
+ * array and starts by clearing what must begin at zero; calls that overlap on
+ * the GPU (other streams, other host threads) race on it and must be
+ * serialised by the caller.  Returns DSDNA_OK or a negative dsdna_status
+ * (EFENE for a broken backbone bond, EOVERFLOW for more than 32 neighbours). */
+#define DSDNA_NOALLOC_MAX_NT 16384
+#define DSDNA_NOALLOC_MAX_MOL 256
+int dsdna_forces_noalloc(const dsdna_params* params, int n_mol, const int* n_bp, const double* X, const double* u,
+                         double* F_bead, double* F_patch, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -277,6 +277,11 @@ static void fill_coef(const dsdna_params& p, Coef<Real>& c) {
   c.rl_max2 = (float)(std::max(rss, rcr) * std::max(rss, rcr));
 }
 
+namespace dsdna {
+// coefficient block of the mixed-precision kernels, for the no-allocation entry point
+__attribute__((visibility("hidden"))) void fill_coef_mixed(const dsdna_params& p, Coef<float>& c) { fill_coef(p, c); }
+}  // namespace dsdna
+
 template <class Real>
 static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
   fill_coef(c->p, a.c);

@@ -62,7 +62,7 @@ class dsdna_info(C.Structure):
 EXPORTS = ["dsdna_default_params", "dsdna_create", "dsdna_set_external_force_torque", "dsdna_step",
            "dsdna_synchronize", "dsdna_energy_virial", "dsdna_observables", "dsdna_get_state", "dsdna_set_state",
            "dsdna_compute_forces", "dsdna_neighbor_pairs", "dsdna_get_info", "dsdna_step_counter",
-           "dsdna_last_error", "dsdna_destroy"]
+           "dsdna_last_error", "dsdna_destroy", "dsdna_forces_noalloc"]
 
 _lib = None
 
@@ -98,6 +98,9 @@ def load(build_if_missing: bool = True):
     L.dsdna_last_error.restype = C.c_char_p
     L.dsdna_destroy.argtypes = [C.c_void_p]
     L.dsdna_destroy.restype = None
+    L.dsdna_forces_noalloc.argtypes = [P(dsdna_params), C.c_int, P(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]
+    L.dsdna_forces_noalloc.restype = C.c_int
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int or name in ("dsdna_create",):
