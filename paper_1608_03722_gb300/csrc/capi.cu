@@ -21,9 +21,12 @@
 namespace dsdna {
 template <class Real> cudaError_t engine_occupancy(int mode, int T, int* blocks_per_sm, size_t* smem);
 template <class Real> cudaError_t engine_launch(int mode, const KArgs<Real>& a, int grid, int T, size_t smem, cudaStream_t st);
+template <class Real> cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st);
 }  // namespace dsdna
 
 using namespace dsdna;
+
+static constexpr int64_t SEG_SLOTS = 32;   // slots per warp segment of the engine kernel
 
 static thread_local std::string g_create_error;
 
@@ -53,6 +56,7 @@ struct dsdna_ctx {
   unsigned long long* nrebuild = nullptr;
   double* fout = nullptr; double* eout = nullptr; double* stage = nullptr;
   double* obs_scratch = nullptr; double* obs_out = nullptr;
+  int64_t* steps_left = nullptr; unsigned* iters = nullptr;
   unsigned H = 0;
   int morton_bits = 0;
   int nc[3] = {0, 0, 0};
@@ -62,9 +66,10 @@ struct dsdna_ctx {
   int64_t nseg = 0;
   int grid[3] = {0, 0, 0};
   size_t smem[3] = {0, 0, 0};
-  cudaGraphExec_t gexec = nullptr;
-  int64_t gsteps = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // step graphs for steps_per_graph and for a remainder
+  int64_t gsteps[2] = {0, 0};
   bool graph_failed = false;
+  int scan_grid = 0;
   int64_t step = 0;
   bool poisoned = false;
   std::string errmsg;
@@ -102,7 +107,8 @@ static void* dalloc(dsdna_ctx* c, size_t bytes) {
 }
 
 static void free_all(dsdna_ctx* c) {
-  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  for (auto& g : c->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   for (void* p : c->bufs) {
     if (c->have_alloc) c->alloc.release(p, c->alloc.user);
     else cudaFree(p);
@@ -285,7 +291,7 @@ __attribute__((visibility("hidden"))) void fill_coef_mixed(const dsdna_params& p
 template <class Real>
 static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
   fill_coef(c->p, a.c);
-  a.n = c->n; a.n_mol = c->n_mol; a.nseg = c->nseg; a.cap = c->p.max_neighbors;
+  a.n = c->n; a.n_mol = c->n_mol; a.nseg = (c->n + SEG_SLOTS - 1) / SEG_SLOTS; a.cap = c->p.max_neighbors;
   a.nsteps = 0; a.noise_mode = c->p.noise;
   a.seed_lo = (uint32_t)c->p.seed; a.seed_hi = (uint32_t)(c->p.seed >> 32);
   a.spin_budget = 4000000000ull;
@@ -299,11 +305,14 @@ static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
     a.L[k] = a.periodic ? c->p.box[k] : 0.0;
     a.Lf[k] = (float)a.L[k];
     a.cellh[k] = (float)(a.periodic ? c->p.box[k] / c->nc[k] : c->cellh);
+    a.invcellh[k] = 1.0f / a.cellh[k];
+    a.invLf[k] = a.periodic ? (float)(1.0 / a.L[k]) : 0.0f;
     a.Lfix[k] = (uint32_t)(uint64_t)llround(a.L[k] * 536870912.0);
   }
   a.mol_off = c->mol_off; a.ext = c->ext_d;
   a.bar = c->bar; a.err = c->err; a.step = c->step_d; a.rebuild = c->rebuild; a.nrebuild = c->nrebuild;
   a.fout = c->fout; a.eout = c->eout;
+  a.steps_left = nullptr; a.use_cond = 0; a.h_while = 0;
 }
 
 static int validate(const dsdna_params* p, const dsdna_system* s) {
@@ -323,9 +332,9 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
   if (p->precision != DSDNA_PREC_MIXED && p->precision != DSDNA_PREC_FP64) return fail(nullptr, DSDNA_EINVAL, "precision");
   if (p->noise < 0 || p->noise > 2) return fail(nullptr, DSDNA_EINVAL, "noise mode");
   if (p->skin < 0.0) return fail(nullptr, DSDNA_EINVAL, "negative skin");
-  if (p->max_neighbors < 0 || p->max_neighbors > 64) return fail(nullptr, DSDNA_EINVAL, "max_neighbors must be <= 64");
-  if (p->block_threads && (p->block_threads < 64 || p->block_threads > 512 || p->block_threads % 32))
-    return fail(nullptr, DSDNA_EINVAL, "block_threads must be a multiple of 32 in [64, 512]");
+  if (p->max_neighbors < 0 || p->max_neighbors > 32) return fail(nullptr, DSDNA_EINVAL, "max_neighbors must be <= 32");
+  if (p->block_threads && (p->block_threads < 64 || p->block_threads > 256 || p->block_threads % 32))
+    return fail(nullptr, DSDNA_EINVAL, "block_threads must be a multiple of 32 in [64, 256]");
   if ((s->X == nullptr) != (s->u == nullptr)) return fail(nullptr, DSDNA_EINVAL, "X and u must be given together");
   if ((s->V == nullptr) != (s->Om == nullptr)) return fail(nullptr, DSDNA_EINVAL, "V and Om must be given together");
   return DSDNA_OK;
@@ -409,7 +418,7 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
       while ((1 << bits) < c->nc[k]) ++bits;
     }
     c->morton_bits = bits;
-    c->H = 1u << (3 * bits);
+    c->H = 1u << (3 * bits);    // one table entry per cell, in Morton order
   } else {
     unsigned H = 1024;
     while ((int64_t)H < 2 * n) H <<= 1;
@@ -441,6 +450,8 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   ALLOC(stage, double, 12 * nn);
   ALLOC(obs_scratch, double, 3 * (size_t)(3 * (c->maxN + 4)));
   ALLOC(obs_out, double, 8);
+  ALLOC(steps_left, int64_t, 1);
+  ALLOC(iters, unsigned, 4);
 #undef ALLOC
   // launch shape per mode (cooperative: every CTA resident)
   int nsm = 0;
@@ -453,7 +464,8 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
     if (c->p.blocks_per_sm > 0) bps = std::min(bps, c->p.blocks_per_sm);
     c->grid[mode] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * nsm, c->nseg));
   }
-  c->bsum = (unsigned*)dalloc(c, sizeof(unsigned) * (size_t)std::max(c->grid[0], std::max(c->grid[1], c->grid[2])));
+  c->scan_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 8, ((int64_t)c->H + 2047) / 2048));
+  c->bsum = (unsigned*)dalloc(c, sizeof(unsigned) * (size_t)c->scan_grid);
   if (!c->bsum) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: bsum"));
 
   // topology flags (Sec. 2; anchored and loaded base pairs of Sec. 4)
@@ -510,19 +522,142 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
 }
 
 // ---------------------------------------------------------------- launches
-static int launch(dsdna_ctx* c, int mode, int64_t nsteps) {
-  CK(cudaMemsetAsync(c->bar, 0, sizeof(GridBar), c->st), "barrier reset");
-  cudaError_t e;
+// Step loop of one graph launch: a WHILE node repeats [head -> IF(rebuild
+// requested) {five rebuild kernels} -> persistent step kernel] until the
+// step kernel reports that the launch's steps are done.
+__global__ void k_loop_init(int64_t* steps_left, int64_t nsteps, unsigned* iters, cudaGraphConditionalHandle h_while) {
+  *steps_left = nsteps;
+  *iters = 0u;
+  cudaGraphSetConditional(h_while, nsteps > 0 ? 1u : 0u);
+}
+
+// The loop continues only if the step kernel of this iteration says so (a
+// step kernel that never runs ends it); more iterations than steps means no
+// progress and ends the loop with a timeout error.
+__global__ void k_loop_head(const int* rebuild, unsigned* iters, unsigned max_iters, unsigned* err, int64_t* steps_left,
+                            cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_if) {
+  const unsigned it = ++*iters;
+  cudaGraphSetConditional(h_while, 0u);
+  bool ok = (*err & B_ERRMASK) == 0;
+  if (it > max_iters) {
+    *steps_left = 0;
+    atomicOr(err, (unsigned)B_ETIMEOUT);
+    ok = false;
+  }
+  cudaGraphSetConditional(h_if, (ok && *rebuild != 0) ? 1u : 0u);
+}
+
+static cudaError_t launch_rebuild(dsdna_ctx* c) {
+  return c->fp64() ? rebuild_launch<double>(c->kd, c->scan_grid, c->st) : rebuild_launch<float>(c->kf, c->scan_grid, c->st);
+}
+
+static cudaError_t launch_engine(dsdna_ctx* c, int mode, int64_t nsteps, int64_t* steps_left, int use_cond,
+                                 cudaGraphConditionalHandle hw) {
+  cudaError_t e = cudaMemsetAsync(c->bar, 0, sizeof(GridBar), c->st);
+  if (e != cudaSuccess) return e;
   if (c->fp64()) {
     KArgs<double> a = c->kd;
-    a.nsteps = nsteps;
-    e = engine_launch<double>(mode, a, c->grid[mode], c->T, c->smem[mode], c->st);
-  } else {
-    KArgs<float> a = c->kf;
-    a.nsteps = nsteps;
-    e = engine_launch<float>(mode, a, c->grid[mode], c->T, c->smem[mode], c->st);
+    a.nsteps = nsteps; a.steps_left = steps_left; a.use_cond = use_cond; a.h_while = hw;
+    return engine_launch<double>(mode, a, c->grid[mode], c->T, c->smem[mode], c->st);
   }
-  if (e != cudaSuccess) return cuda_fail(c, e, "engine launch");
+  KArgs<float> a = c->kf;
+  a.nsteps = nsteps; a.steps_left = steps_left; a.use_cond = use_cond; a.h_while = hw;
+  return engine_launch<float>(mode, a, c->grid[mode], c->T, c->smem[mode], c->st);
+}
+
+// force / energy pass on a fresh list
+static int launch(dsdna_ctx* c, int mode, int64_t nsteps) {
+  CK(launch_rebuild(c), "rebuild launch");
+  CK(launch_engine(c, mode, nsteps, nullptr, 0, 0), "engine launch");
+  return DSDNA_OK;
+}
+
+static cudaError_t build_step_graph(dsdna_ctx* c, int64_t K, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  auto done = [&](cudaError_t err) {
+    if (g) cudaGraphDestroy(g);
+    return err;
+  };
+  cudaGraphConditionalHandle hw = 0, hi = 0;
+  if ((e = cudaGraphConditionalHandleCreate(&hw, g, 0, 0)) != cudaSuccess) return done(e);
+  if ((e = cudaGraphConditionalHandleCreate(&hi, g, 0, 0)) != cudaSuccess) return done(e);
+  cudaGraphNode_t init = nullptr, head = nullptr, wn = nullptr, ifn = nullptr;
+  {
+    int64_t* sl = c->steps_left;
+    unsigned* it = c->iters;
+    int64_t k = K;
+    void* args[] = {&sl, &k, &it, &hw};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k_loop_init;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    if ((e = cudaGraphAddKernelNode(&init, g, nullptr, 0, &kp)) != cudaSuccess) return done(e);
+  }
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&wn, g, &init, nullptr, 1, &wp)) != cudaSuccess) return done(e);
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  {
+    int* rb = c->rebuild;
+    unsigned* it = c->iters;
+    unsigned maxit = (unsigned)(K + 2);
+    unsigned* er = c->err;
+    int64_t* sl = c->steps_left;
+    void* args[] = {&rb, &it, &maxit, &er, &sl, &hw, &hi};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)k_loop_head;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    if ((e = cudaGraphAddKernelNode(&head, body, nullptr, 0, &kp)) != cudaSuccess) return done(e);
+  }
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hi;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&ifn, body, &head, nullptr, 1, &ip)) != cudaSuccess) return done(e);
+  cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(c->st, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return done(e);
+  cudaError_t e1 = launch_rebuild(c);
+  cudaError_t e2 = cudaStreamEndCapture(c->st, &ifbody);
+  if (e1 != cudaSuccess) return done(e1);
+  if (e2 != cudaSuccess) return done(e2);
+  if ((e = cudaStreamBeginCaptureToGraph(c->st, body, &ifn, nullptr, 1, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return done(e);
+  e1 = launch_engine(c, MODE_STEP, K, c->steps_left, 1, hw);
+  e2 = cudaStreamEndCapture(c->st, &body);
+  if (e1 != cudaSuccess) return done(e1);
+  if (e2 != cudaSuccess) return done(e2);
+  e = cudaGraphInstantiate(out, g, 0);
+  return done(e);
+}
+
+// Fallback without conditional graph nodes: the host waits after every
+// persistent launch and queues the rebuild itself.
+static int step_host_loop(dsdna_ctx* c, int64_t nsteps) {
+  int64_t dstep = 0;
+  CK(cudaStreamSynchronize(c->st), "step sync");
+  CK(cudaMemcpy(&dstep, c->step_d, sizeof(dstep), cudaMemcpyDeviceToHost), "read step");
+  const int64_t target = dstep + nsteps;
+  for (int guard = 0; guard < nsteps + 2; ++guard) {
+    int rb = 0;
+    unsigned er = 0;
+    CK(cudaMemcpy(&dstep, c->step_d, sizeof(dstep), cudaMemcpyDeviceToHost), "read step");
+    CK(cudaMemcpy(&rb, c->rebuild, sizeof(rb), cudaMemcpyDeviceToHost), "read rebuild flag");
+    CK(cudaMemcpy(&er, c->err, sizeof(er), cudaMemcpyDeviceToHost), "read error word");
+    if (er || dstep >= target) break;
+    if (rb) CK(launch_rebuild(c), "rebuild launch");
+    CK(launch_engine(c, MODE_STEP, target - dstep, nullptr, 0, 0), "engine launch");
+    CK(cudaStreamSynchronize(c->st), "step sync");
+  }
   return DSDNA_OK;
 }
 
@@ -567,29 +702,26 @@ extern "C" int dsdna_step(dsdna_ctx* c, int64_t nsteps) {
   const int64_t K = c->p.steps_per_graph;
   while (nsteps > 0) {
     const int64_t chunk = std::min(nsteps, K);
-    if (chunk == K && !c->graph_failed) {
-      if (!c->gexec) {
-        cudaGraph_t g = nullptr;
-        bool ok = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        if (ok) {
-          const int rc = launch(c, MODE_STEP, K);
-          cudaError_t e2 = cudaStreamEndCapture(c->st, &g);
-          ok = (rc == DSDNA_OK) && e2 == cudaSuccess && g != nullptr;
-          if (ok) ok = cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess;
-          if (g) cudaGraphDestroy(g);
-          c->poisoned = false;
-          c->errmsg.clear();
+    if (!c->graph_failed) {
+      const int slot = chunk == K ? 0 : 1;
+      if (!c->gexec[slot] || c->gsteps[slot] != chunk) {
+        if (c->gexec[slot]) { cudaGraphExecDestroy(c->gexec[slot]); c->gexec[slot] = nullptr; }
+        if (build_step_graph(c, chunk, &c->gexec[slot]) == cudaSuccess) {
+          c->gsteps[slot] = chunk;
+        } else {
+          c->gexec[slot] = nullptr;
+          c->graph_failed = true;
+          cudaGetLastError();
         }
-        if (!ok) { c->graph_failed = true; c->gexec = nullptr; cudaGetLastError(); }
       }
-      if (c->gexec) {
-        CK(cudaGraphLaunch(c->gexec, c->st), "graph launch");
+      if (c->gexec[slot]) {
+        CK(cudaGraphLaunch(c->gexec[slot], c->st), "graph launch");
         c->step += chunk;
         nsteps -= chunk;
         continue;
       }
     }
-    int rc = launch(c, MODE_STEP, chunk);
+    int rc = step_host_loop(c, chunk);
     if (rc) return rc;
     c->step += chunk;
     nsteps -= chunk;
@@ -717,8 +849,6 @@ extern "C" int dsdna_compute_forces(dsdna_ctx* c, double* Fb, double* Fp) {
 extern "C" int dsdna_neighbor_pairs(dsdna_ctx* c, int64_t cap, int64_t* pi, int64_t* pj, int64_t* count) {
   if (!c || !count) return DSDNA_EINVAL;
   if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
-  const int one = 1;
-  CK(cudaMemcpyAsync(c->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, c->st), "request rebuild");
   int rc = launch(c, MODE_FORCES, 0);
   if (rc) return rc;
   rc = sync_check(c);

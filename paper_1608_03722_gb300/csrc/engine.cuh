@@ -97,7 +97,9 @@ struct KArgs {
   int periodic;
   int nc[3];
   float cellh[3];
+  float invcellh[3];
   float Lf[3];
+  float invLf[3];
   double L[3];
   unsigned Lfix[3];
   // molecules
@@ -112,6 +114,10 @@ struct KArgs {
   // outputs
   double* fout;    // MODE_FORCES: [n][6]
   double* eout;    // MODE_ENERGY: [n_mol][16]
+  // step loop in a CUDA graph (conditional WHILE/IF nodes)
+  int64_t* steps_left;              // steps still to run in this graph launch (null: run nsteps)
+  int use_cond;
+  cudaGraphConditionalHandle h_while;
 };
 
 // ---------------------------------------------------------------- small vectors
@@ -208,11 +214,39 @@ __device__ __forceinline__ V3<double> rel(const SPos<double>& o, const SPos<doub
 }
 template <class Real> __device__ __forceinline__ V3<Real> uvec(const SPos<Real>& s) { return V3<Real>{s.ux, s.uy, s.uz}; }
 
-// low 32 bits of round(x * 2^29): the exponent of 1.5 * 2^52 + x 2^29 puts
-// the integer part in the low mantissa bits (|x| < 2^22 nm)
+// Low 32 bits of round(x * 2^29) (ties away from zero), from the bits of x
+// with integer operations only: the FP64 pipe of GB300 runs at a small
+// fraction of the integer rate.  Valid for |x| < 2^33 nm.
 __device__ __forceinline__ int fix32(double x) {
-  const double t = fma(x, 536870912.0, 6755399441055744.0);
-  return (int)(unsigned)__double_as_longlong(t);
+  const long long b = __double_as_longlong(x);
+  const int sh = 1046 - (int)((b >> 52) & 0x7FF);          // right shift of the 53-bit significand
+  if (sh > 53) return 0;                                    // |x| < 2^-30 rounds to zero
+  const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  const unsigned long long r = sh > 0 ? (m + (1ull << (sh - 1))) >> sh : m << (-sh);
+  const unsigned lo = (unsigned)r;
+  return b < 0 ? (int)(0u - lo) : (int)lo;
+}
+
+// FP64 -> FP32 (round to nearest even) and FP32 -> FP64 (exact) by integer
+// operations on the bit patterns, for the FP32 arithmetic around the FP64
+// accumulators.  Magnitudes below the smallest normal FP32 flush to zero;
+// the callers' values (velocities, their increments) stay far inside the
+// normal range.
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  if (a < 0x3810000000000000ull) return __uint_as_float(sign);
+  const unsigned long long t = a - 0x3800000000000000ull;  // rebias the exponent 1023 -> 127
+  const unsigned long long r = (t + 0x0FFFFFFFull + ((t >> 29) & 1ull)) >> 29;
+  return __uint_as_float((unsigned)r | sign);
+}
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned a = u & 0x7FFFFFFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (a < 0x00800000u) return __longlong_as_double((long long)sign);
+  return __longlong_as_double((long long)((((unsigned long long)a << 29) + 0x3800000000000000ull) | sign));
 }
 
 // bead offset -h u on the fixed-point grid (rebuild trigger only)

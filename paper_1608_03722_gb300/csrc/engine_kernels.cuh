@@ -9,35 +9,54 @@ namespace dsdna {
 // ---------------------------------------------------------------- shared memory
 template <class Real>
 struct SegSmem {
-  SPos<Real>* pos;   // [T + 8]  slots base-4 .. base+T+3
-  int* flg;          // [T + 8]
-  Real* cs;          // [T + 4][6] forces of owner terms on the owner (bead xyz, patch xyz)
-  Real* cn;          // [T + 4][6] ... on the owner's next nucleotide
-  Real* cp;          // [T + 4][3] ... on the owner's previous patch (bending)
+  SPos<Real>* pos;   // [W + 8]  slots base-4 .. base+W+3
+  int* flg;          // [W + 8]
+  Real* cs;          // [W + 4][6] forces of owner terms on the owner (bead xyz, patch xyz)
+  Real* cn;          // [W + 4][6] ... on the owner's next nucleotide
+  Real* cp;          // [W + 4][3] ... on the owner's previous patch (bending)
 };
 
+// Each warp owns a segment of SEG = 32 slots and a private slice of shared
+// memory, so the segment pass synchronises with __syncwarp only.
+constexpr int SEG = 32;
+
 template <class Real>
-__host__ __device__ inline size_t seg_smem_bytes(int T) {
-  size_t b = sizeof(SPos<Real>) * (T + 8) + sizeof(int) * (T + 8);
+__host__ __device__ inline size_t seg_warp_bytes() {
+  size_t b = sizeof(SPos<Real>) * (SEG + 8) + sizeof(int) * (SEG + 8);
   b = (b + 15) & ~(size_t)15;
-  b += sizeof(Real) * (size_t)(T + 4) * 15;
-  return b + 64;
+  b += sizeof(Real) * (size_t)(SEG + 4) * 15;
+  return (b + 15) & ~(size_t)15;
 }
 
 template <class Real>
-__device__ __forceinline__ SegSmem<Real> carve(unsigned char* raw, int T) {
+__host__ __device__ inline size_t seg_smem_bytes(int T) {
+  return seg_warp_bytes<Real>() * (size_t)(T / 32) + 64;
+}
+
+template <class Real>
+__device__ __forceinline__ SegSmem<Real> carve(unsigned char* raw, int /*T*/) {
+  unsigned char* w = raw + seg_warp_bytes<Real>() * (threadIdx.x >> 5);
   SegSmem<Real> s;
-  s.pos = reinterpret_cast<SPos<Real>*>(raw);
-  s.flg = reinterpret_cast<int*>(raw + sizeof(SPos<Real>) * (T + 8));
-  size_t off = sizeof(SPos<Real>) * (T + 8) + sizeof(int) * (T + 8);
+  s.pos = reinterpret_cast<SPos<Real>*>(w);
+  s.flg = reinterpret_cast<int*>(w + sizeof(SPos<Real>) * (SEG + 8));
+  size_t off = sizeof(SPos<Real>) * (SEG + 8) + sizeof(int) * (SEG + 8);
   off = (off + 15) & ~(size_t)15;
-  s.cs = reinterpret_cast<Real*>(raw + off);
-  s.cn = s.cs + (size_t)(T + 4) * 6;
-  s.cp = s.cn + (size_t)(T + 4) * 6;
+  s.cs = reinterpret_cast<Real*>(w + off);
+  s.cn = s.cs + (size_t)(SEG + 4) * 6;
+  s.cp = s.cn + (size_t)(SEG + 4) * 6;
   return s;
 }
 
 // ---------------------------------------------------------------- cell hash
+__device__ __forceinline__ unsigned compact3(unsigned v) {  // every third bit -> 10 bits
+  v &= 0x09249249u;
+  v = (v | (v >> 2)) & 0x030C30C3u;
+  v = (v | (v >> 4)) & 0x0300F00Fu;
+  v = (v | (v >> 8)) & 0x030000FFu;
+  v = (v | (v >> 16)) & 0x000003FFu;
+  return v;
+}
+
 __device__ __forceinline__ unsigned spread3(unsigned v) {   // 10 bits -> every third bit
   v &= 0x3ffu;
   v = (v | (v << 16)) & 0x030000FFu;
@@ -56,6 +75,21 @@ __device__ __forceinline__ unsigned cell_key(const KArgs<Real>& a, int mol, int 
                (unsigned)mol * 0x9E3779B1u;
   h ^= h >> 16; h *= 0x7feb352du; h ^= h >> 15; h *= 0x846ca68bu; h ^= h >> 16;
   return h & (a.H - 1u);
+}
+
+template <class Real>
+__device__ __forceinline__ void bead_position_f(const KArgs<Real>& a, int cur, int64_t g, float* b) {
+  const float h = (float)a.c.h;
+  if constexpr (sizeof(Real) == 4) {
+    const float4 u = a.U[(size_t)cur * a.n + g];
+    b[0] = d2f_bits(a.X[g]) - h * u.x;
+    b[1] = d2f_bits(a.X[a.n + g]) - h * u.y;
+    b[2] = d2f_bits(a.X[2 * a.n + g]) - h * u.z;
+  } else {
+    const double* X = a.X + (size_t)cur * 3 * a.n;
+    const double* u = a.ud + (size_t)cur * 3 * a.n;
+    for (int c = 0; c < 3; ++c) b[c] = (float)(X[c * a.n + g] - (double)h * u[c * a.n + g]);
+  }
 }
 
 template <class Real>
@@ -78,26 +112,26 @@ template <class Real>
 __device__ void rebuild_bin(const KArgs<Real>& a, int cur, unsigned& fl) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.n; g += stride) {
-    double b[3];
-    bead_position(a, cur, g, b);
+    // Binning in FP32: any integer image w with pw = b - w L is exact for the
+    // force path (it only uses integer image differences), so rounding here
+    // moves a bead by at most a few 1e-5 nm inside the 0.01 nm list margin.
+    float b[3];
+    bead_position_f(a, cur, g, b);
     int w[3] = {0, 0, 0}, ci[3];
     float pw[3];
     for (int c = 0; c < 3; ++c) {
-      double x = b[c];
-      if (a.periodic && a.L[c] > 0.0) {
-        const double q = floor(x / a.L[c]);
+      float x = b[c];
+      if (a.periodic) {
+        const float q = floorf(x * a.invLf[c]);
         w[c] = (int)q;
-        x -= q * a.L[c];
-        float xf = (float)x;
-        if (xf >= a.Lf[c]) xf = 0.0f;
-        if (xf < 0.0f) xf = 0.0f;
-        pw[c] = xf;
-        int k = (int)(xf / a.cellh[c]);
-        ci[c] = k >= a.nc[c] ? a.nc[c] - 1 : k;
+        x = fmaf(-q, a.Lf[c], x);
+        pw[c] = x;
+        int k = (int)floorf(x * a.invcellh[c]);
+        ci[c] = k >= a.nc[c] ? a.nc[c] - 1 : (k < 0 ? 0 : k);
         if (w[c] > 511 || w[c] < -512) fl |= B_EIMG;
       } else {
-        pw[c] = (float)x;
-        ci[c] = (int)floorf(pw[c] / a.cellh[c]);
+        pw[c] = x;
+        ci[c] = (int)floorf(x * a.invcellh[c]);
       }
     }
     const int packed = (w[0] & 0x3ff) | ((w[1] & 0x3ff) << 10) | ((w[2] & 0x3ff) << 20);
@@ -152,13 +186,28 @@ __device__ __forceinline__ unsigned block_exscan(unsigned v, unsigned* s_warp, u
   return before;
 }
 
-// R2a: per-block sums of the count table
+// R2a: per-block sums of the count table.  The table is split into chunks
+// of whole 2048-entry tiles (256 threads x 8 entries, two 16-byte loads each).
+constexpr unsigned SCAN_ITEMS = 8;
+
+__device__ __forceinline__ void scan_chunk(unsigned H, unsigned* lo, unsigned* hi) {
+  const unsigned tile = blockDim.x * SCAN_ITEMS;
+  const unsigned ntile = (H + tile - 1) / tile;
+  const unsigned per = (ntile + gridDim.x - 1) / gridDim.x;
+  *lo = min(H, blockIdx.x * per * tile);
+  *hi = min(H, (blockIdx.x + 1) * per * tile);
+}
+
 template <class Real>
 __device__ void rebuild_scan_a(const KArgs<Real>& a, unsigned* s_red) {
-  const unsigned chunk = (a.H + gridDim.x - 1) / gridDim.x;
-  const unsigned lo = blockIdx.x * chunk, hi = min(a.H, lo + chunk);
+  unsigned lo, hi;
+  scan_chunk(a.H, &lo, &hi);
   unsigned s = 0;
-  for (unsigned i = lo + threadIdx.x; i < hi; i += blockDim.x) s += a.cnt[i];
+  for (unsigned i = lo + threadIdx.x * SCAN_ITEMS; i < hi; i += blockDim.x * SCAN_ITEMS) {
+    const uint4 x = *reinterpret_cast<const uint4*>(a.cnt + i);
+    const uint4 y = *reinterpret_cast<const uint4*>(a.cnt + i + 4);
+    s += x.x + x.y + x.z + x.w + y.x + y.y + y.z + y.w;
+  }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -173,8 +222,8 @@ __device__ void rebuild_scan_a(const KArgs<Real>& a, unsigned* s_red) {
 // R2b: exclusive scan -> start[]
 template <class Real>
 __device__ void rebuild_scan_b(const KArgs<Real>& a, unsigned* s_red) {
-  const unsigned chunk = (a.H + gridDim.x - 1) / gridDim.x;
-  const unsigned lo = blockIdx.x * chunk, hi = min(a.H, lo + chunk);
+  unsigned lo, hi;
+  scan_chunk(a.H, &lo, &hi);
   unsigned pre = 0;
   for (unsigned b = threadIdx.x; b < blockIdx.x; b += blockDim.x) pre += a.bsum[b];
   for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
@@ -183,12 +232,23 @@ __device__ void rebuild_scan_b(const KArgs<Real>& a, unsigned* s_red) {
   unsigned carry = 0;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) carry += s_red[w];
   __syncthreads();
-  for (unsigned base = lo; base < hi; base += blockDim.x) {
-    const unsigned i = base + threadIdx.x;
-    const unsigned v = i < hi ? a.cnt[i] : 0u;
+  for (unsigned base = lo; base < hi; base += blockDim.x * SCAN_ITEMS) {
+    const unsigned i = base + threadIdx.x * SCAN_ITEMS;
+    uint4 x = make_uint4(0, 0, 0, 0), y = make_uint4(0, 0, 0, 0);
+    if (i < hi) {
+      x = *reinterpret_cast<const uint4*>(a.cnt + i);
+      y = *reinterpret_cast<const uint4*>(a.cnt + i + 4);
+    }
+    const unsigned v = x.x + x.y + x.z + x.w + y.x + y.y + y.z + y.w;
     unsigned tot;
-    const unsigned ex = block_exscan(v, s_red, &tot);
-    if (i < hi) a.start[i] = carry + ex;
+    unsigned r = carry + block_exscan(v, s_red, &tot);
+    if (i < hi) {
+      uint4 o1, o2;
+      o1.x = r; r += x.x; o1.y = r; r += x.y; o1.z = r; r += x.z; o1.w = r; r += x.w;
+      o2.x = r; r += y.x; o2.y = r; r += y.y; o2.z = r; r += y.z; o2.w = r;
+      *reinterpret_cast<uint4*>(a.start + i) = o1;
+      *reinterpret_cast<uint4*>(a.start + i + 4) = o2;
+    }
     carry += tot;
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) a.start[a.H] = (unsigned)a.n;
@@ -203,82 +263,293 @@ __device__ void rebuild_scatter(const KArgs<Real>& a) {
     const unsigned k = (unsigned)a.key[g];
     const unsigned slot = a.start[k] + atomicSub(&a.cnt[k], 1u) - 1u;
     const float4 w = a.wpos[g];
-    a.cent[slot] = make_float4(w.x, w.y, w.z, __int_as_float((int)g));
+    const int st = (a.topo[g] & F_STERIC) ? (1 << NBR_J_BITS) : 0;
+    a.cent[slot] = make_float4(w.x, w.y, w.z, __int_as_float((int)g | st));
   }
 }
 
 // R4: typed full neighbour list of every bead, sorted by partner slot.
 // Pairs (Sec. 2, reading A1): opposite strands always (sigma_cross); same
-// strand only steric-steric (sigma_ss); same molecule only.
+// strand only steric-steric (sigma_ss); same molecule only.  Beads are taken
+// in cell order (Morton order in a periodic box).  The 27 neighbour cells are
+// read one 3x3 layer at a time so that nine range loads are in flight at once.
 template <class Real, int CAPMAX>
-__device__ void rebuild_list(const KArgs<Real>& a, unsigned& fl) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
+__device__ void list_one_bead(const KArgs<Real>& a, int64_t t, unsigned& fl) {
+  const int JMASK = (1 << NBR_J_BITS) - 1;
+  const bool dedupe = !(a.morton_bits > 0 && a.nc[0] >= 3 && a.nc[1] >= 3 && a.nc[2] >= 3);
+  {
     const float4 me = a.cent[t];
-    const int g = __float_as_int(me.w);
-    const int mol = __float_as_int(a.wpos[g].w);
-    const bool st_g = (a.topo[g] & F_STERIC) != 0;
+    const int gw = __float_as_int(me.w);
+    const int g = gw & JMASK;
+    const bool st_g = (gw >> NBR_J_BITS) & 1;
+    const int mol = a.n_mol > 1 ? __float_as_int(a.wpos[g].w) : 0;
     int ci[3];
     const float p[3] = {me.x, me.y, me.z};
     for (int c = 0; c < 3; ++c) {
-      int k = (int)floorf(p[c] / a.cellh[c]);
-      if (a.periodic && a.L[c] > 0.0 && k >= a.nc[c]) k = a.nc[c] - 1;
+      int k = (int)floorf(p[c] * a.invcellh[c]);
+      if (a.periodic) k = k >= a.nc[c] ? a.nc[c] - 1 : (k < 0 ? 0 : k);
       ci[c] = k;
     }
     int list[CAPMAX];
     int cnt = 0, total = 0;
     unsigned seen[27];
     int nseen = 0;
-    const bool dedupe = !(a.morton_bits > 0 && a.nc[0] >= 3 && a.nc[1] >= 3 && a.nc[2] >= 3);
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          int c3[3] = {ci[0] + dx, ci[1] + dy, ci[2] + dz};
+    for (int dz = -1; dz <= 1; ++dz) {
+      unsigned kk[9], b0[9], b1[9];
+      bool use[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        int c3[3] = {ci[0] + (q % 3) - 1, ci[1] + (q / 3) - 1, ci[2] + dz};
+        if (a.periodic)
+          for (int c = 0; c < 3; ++c) c3[c] = c3[c] < 0 ? c3[c] + a.nc[c] : (c3[c] >= a.nc[c] ? c3[c] - a.nc[c] : c3[c]);
+        kk[q] = cell_key(a, mol, c3[0], c3[1], c3[2]);
+        use[q] = true;
+        if (dedupe) {
+          for (int r = 0; r < nseen; ++r) use[q] = use[q] && (seen[r] != kk[q]);
+          if (use[q]) seen[nseen++] = kk[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        b0[q] = use[q] ? a.start[kk[q]] : 0u;
+        b1[q] = use[q] ? a.start[kk[q] + 1] : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        for (unsigned e = b0[q]; e < b1[q]; ++e) {
+          const float4 o = a.cent[e];
+          const int jw = __float_as_int(o.w);
+          const int j = jw & JMASK;
+          if (j == g) continue;
+          float d[3] = {o.x - p[0], o.y - p[1], o.z - p[2]};
+          int sc[3] = {0, 0, 0};
           if (a.periodic)
-            for (int c = 0; c < 3; ++c)
-              if (a.L[c] > 0.0) c3[c] = (c3[c] % a.nc[c] + a.nc[c]) % a.nc[c];
-          const unsigned k = cell_key(a, mol, c3[0], c3[1], c3[2]);
-          if (dedupe) {
-            bool dup = false;
-            for (int q = 0; q < nseen; ++q) dup |= (seen[q] == k);
-            if (dup) continue;
-            seen[nseen++] = k;
-          }
-          const unsigned e1 = a.start[k + 1];
-          for (unsigned e = a.start[k]; e < e1; ++e) {
-            const float4 o = a.cent[e];
-            const int j = __float_as_int(o.w);
-            if (j == g) continue;
-            float d[3] = {o.x - p[0], o.y - p[1], o.z - p[2]};
-            int sc[3] = {0, 0, 0};
-            if (a.periodic)
-              for (int c = 0; c < 3; ++c)
-                if (a.L[c] > 0.0) {
-                  const float s = -rintf(d[c] / a.Lf[c]);
-                  d[c] += s * a.Lf[c];
-                  sc[c] = (int)s;
-                }
-            const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (r2 >= a.c.rl_max2) continue;
-            if (__float_as_int(a.wpos[j].w) != mol) continue;
-            float rl2;
-            if ((g ^ j) & 1) rl2 = a.c.rl_cr2;
-            else if (st_g && (a.topo[j] & F_STERIC)) rl2 = a.c.rl_ss2;
-            else continue;
-            if (r2 >= rl2) continue;
-            const int code = (sc[0] + 1) + 3 * (sc[1] + 1) + 9 * (sc[2] + 1);
-            const int ent = j | (code << NBR_J_BITS);
-            ++total;
-            if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed
-              int q = cnt++;
-              while (q > 0 && (list[q - 1] & ((1 << NBR_J_BITS) - 1)) > j) { list[q] = list[q - 1]; --q; }
-              list[q] = ent;
+            for (int c = 0; c < 3; ++c) {
+              const float s = -rintf(d[c] * a.invLf[c]);
+              d[c] = fmaf(s, a.Lf[c], d[c]);
+              sc[c] = (int)s;
             }
+          const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+          float rl2;
+          if ((g ^ j) & 1) rl2 = a.c.rl_cr2;
+          else if (st_g && ((jw >> NBR_J_BITS) & 1)) rl2 = a.c.rl_ss2;
+          else continue;
+          if (r2 >= rl2) continue;
+          if (a.n_mol > 1 && __float_as_int(a.wpos[j].w) != mol) continue;
+          const int code = (sc[0] + 1) + 3 * (sc[1] + 1) + 9 * (sc[2] + 1);
+          const int ent = j | (code << NBR_J_BITS);
+          ++total;
+          if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed
+            int qq = cnt++;
+            while (qq > 0 && (list[qq - 1] & JMASK) > j) { list[qq] = list[qq - 1]; --qq; }
+            list[qq] = ent;
           }
         }
+      }
+    }
     if (total > a.cap) fl |= B_EOVF;
     for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.n + g] = list[q];
     a.ncnt[g] = cnt;
+  }
+}
+
+// Typed pair test of bead (p, g) against candidate o; appends to the sorted list.
+template <class Real, int CAPMAX>
+__device__ __forceinline__ void consider(const KArgs<Real>& a, const float* p, int g, bool st_g, int mol, float4 o,
+                                         int* list, int& cnt, int& total) {
+  const int JMASK = (1 << NBR_J_BITS) - 1;
+  const int jw = __float_as_int(o.w);
+  const int j = jw & JMASK;
+  if (j == g) return;
+  float d[3] = {o.x - p[0], o.y - p[1], o.z - p[2]};
+  int sc[3] = {0, 0, 0};
+  if (a.periodic)
+    for (int c = 0; c < 3; ++c) {
+      const float s = -rintf(d[c] * a.invLf[c]);
+      d[c] = fmaf(s, a.Lf[c], d[c]);
+      sc[c] = (int)s;
+    }
+  const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  float rl2;
+  if ((g ^ j) & 1) rl2 = a.c.rl_cr2;
+  else if (st_g && ((jw >> NBR_J_BITS) & 1)) rl2 = a.c.rl_ss2;
+  else return;
+  if (r2 >= rl2) return;
+  if (a.n_mol > 1 && __float_as_int(a.wpos[j].w) != mol) return;
+  const int ent = j | (((sc[0] + 1) + 3 * (sc[1] + 1) + 9 * (sc[2] + 1)) << NBR_J_BITS);
+  ++total;
+  if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed
+    int q = cnt++;
+    while (q > 0 && (list[q - 1] & JMASK) > j) { list[q] = list[q - 1]; --q; }
+    list[q] = ent;
+  }
+}
+
+// R4 (warp per table entry): the beads of one cell share one neighbourhood.
+// Lanes 0..26 read the ranges of the 27 neighbour cells at once, the warp
+// stages their beads in shared memory in tiles of LIST_TILE, and all 32 lanes
+// share the pair tests of up to LIST_CB beads of the cell against the tile;
+// hits go to per-bead shared buffers that the bead's lane sorts by partner
+// slot before writing its list.  Entries whose beads belong to several cells
+// (hash collisions) take the per-bead path.
+constexpr int LIST_TILE = 128;
+constexpr int LIST_WARPS = 8;
+constexpr int LIST_CB = 16;
+constexpr int LIST_CAP = 32;
+
+// typed pair test; returns the list entry, or -1 (no entry has all bits set:
+// image codes stop at 26) -- entries with codes >= 16 are negative ints
+template <class Real>
+__device__ __forceinline__ int pair_entry(const KArgs<Real>& a, float4 me, float4 o, int mol) {
+  const int JMASK = (1 << NBR_J_BITS) - 1;
+  const int gw = __float_as_int(me.w), jw = __float_as_int(o.w);
+  const int g = gw & JMASK, j = jw & JMASK;
+  if (j == g) return -1;
+  float rl2;
+  if ((g ^ j) & 1) rl2 = a.c.rl_cr2;
+  else if (((gw & jw) >> NBR_J_BITS) & 1) rl2 = a.c.rl_ss2;
+  else return -1;
+  float d[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
+  int code = 13;
+  if (a.periodic) {
+    code = 0;
+    const int mul[3] = {1, 3, 9};
+    for (int c = 0; c < 3; ++c) {
+      const float s = -rintf(d[c] * a.invLf[c]);
+      d[c] = fmaf(s, a.Lf[c], d[c]);
+      code += ((int)s + 1) * mul[c];
+    }
+  }
+  if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] >= rl2) return -1;
+  if (a.n_mol > 1 && __float_as_int(a.wpos[j].w) != mol) return -1;
+  return j | (code << NBR_J_BITS);
+}
+
+template <class Real, int CAPMAX>
+__device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
+  __shared__ float4 tile[LIST_WARPS][LIST_TILE];
+  __shared__ float4 cpos[LIST_WARPS][LIST_CB];
+  __shared__ int scount[LIST_WARPS][LIST_CB];
+  __shared__ int sent[LIST_WARPS][LIST_CB][LIST_CAP];
+  __shared__ unsigned rb[LIST_WARPS][28], roff[LIST_WARPS][28];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int JMASK = (1 << NBR_J_BITS) - 1;
+  const bool dedupe = !(a.morton_bits > 0 && a.nc[0] >= 3 && a.nc[1] >= 3 && a.nc[2] >= 3);
+  const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
+  const unsigned wid = blockIdx.x * (blockDim.x >> 5) + w;
+  for (unsigned kb = wid * 32u; kb < a.H; kb += nwarps * 32u) {
+    const unsigned k0 = kb + lane;
+    const unsigned s0 = k0 < a.H ? a.start[k0] : 0u, s1 = k0 < a.H ? a.start[k0 + 1] : 0u;
+    unsigned busy = __ballot_sync(0xffffffffu, s1 > s0);
+    while (busy) {
+      const int src = __ffs(busy) - 1;
+      busy &= busy - 1;
+      const unsigned beg = __shfl_sync(0xffffffffu, s0, src), end = __shfl_sync(0xffffffffu, s1, src);
+      int c0[3];
+      int mol0 = 0;
+      bool same = true;
+      if (a.morton_bits > 0 && a.n_mol == 1) {
+        // one molecule in a periodic box: the table entry is exactly one cell
+        const unsigned kc = kb + (unsigned)src;
+        c0[0] = (int)compact3(kc); c0[1] = (int)compact3(kc >> 1); c0[2] = (int)compact3(kc >> 2);
+      } else {
+      // the cell of the entry's first bead; all beads must share it
+      const float4 f0 = a.cent[beg];
+      for (int c = 0; c < 3; ++c) {
+        const float q = c == 0 ? f0.x : (c == 1 ? f0.y : f0.z);
+        int kk = (int)floorf(q * a.invcellh[c]);
+        if (a.periodic) kk = kk >= a.nc[c] ? a.nc[c] - 1 : (kk < 0 ? 0 : kk);
+        c0[c] = kk;
+      }
+      mol0 = a.n_mol > 1 ? __float_as_int(a.wpos[__float_as_int(f0.w) & JMASK].w) : 0;
+      for (unsigned t = beg + lane; t < end; t += 32) {
+        const float4 f = a.cent[t];
+        for (int c = 0; c < 3; ++c) {
+          const float q = c == 0 ? f.x : (c == 1 ? f.y : f.z);
+          int kk = (int)floorf(q * a.invcellh[c]);
+          if (a.periodic) kk = kk >= a.nc[c] ? a.nc[c] - 1 : (kk < 0 ? 0 : kk);
+          same = same && kk == c0[c];
+        }
+        if (a.n_mol > 1) same = same && __float_as_int(a.wpos[__float_as_int(f.w) & JMASK].w) == mol0;
+      }
+      }
+      if (!__all_sync(0xffffffffu, same)) {
+        for (unsigned t = beg + lane; t < end; t += 32) list_one_bead<Real, CAPMAX>(a, (int64_t)t, fl);
+        continue;
+      }
+      // ranges of the 27 neighbour cells, one per lane, duplicates (hash) dropped
+      unsigned rbeg = 0, rlen = 0, key = 0xffffffffu;
+      if (lane < 27) {
+        int c3[3] = {c0[0] + (lane % 3) - 1, c0[1] + (lane / 3) % 3 - 1, c0[2] + lane / 9 - 1};
+        if (a.periodic)
+          for (int c = 0; c < 3; ++c) c3[c] = c3[c] < 0 ? c3[c] + a.nc[c] : (c3[c] >= a.nc[c] ? c3[c] - a.nc[c] : c3[c]);
+        key = cell_key(a, mol0, c3[0], c3[1], c3[2]);
+      }
+      if (dedupe) {
+        for (int o = 0; o < 27; ++o) {
+          const unsigned ko = __shfl_sync(0xffffffffu, key, o);
+          if (o < lane && ko == key) key = 0xffffffffu;
+        }
+      }
+      if (lane < 27 && key != 0xffffffffu) {
+        rbeg = a.start[key];
+        rlen = a.start[key + 1] - rbeg;
+      }
+      unsigned incl = rlen;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned M = __shfl_sync(0xffffffffu, incl, 31);
+      if (lane < 27) { rb[w][lane] = rbeg; roff[w][lane] = incl - rlen; }
+      __syncwarp();
+      for (unsigned cb = beg; cb < end; cb += LIST_CB) {
+        const int mc = (int)min((unsigned)LIST_CB, end - cb);
+        if (lane < mc) { cpos[w][lane] = a.cent[cb + lane]; scount[w][lane] = 0; }
+        for (unsigned m0 = 0; m0 < M; m0 += LIST_TILE) {
+          const unsigned mn = min((unsigned)LIST_TILE, M - m0);
+          __syncwarp();
+          for (unsigned i = lane; i < mn; i += 32) {
+            const unsigned gi = m0 + i;
+            int lo = 0, hi = 26;   // last neighbour cell whose staged range starts at or before gi
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (roff[w][mid] <= gi) lo = mid; else hi = mid - 1;
+            }
+            tile[w][i] = a.cent[rb[w][lo] + (gi - roff[w][lo])];
+          }
+          __syncwarp();
+          // all lanes: bead b of the cell against tile entries i = lane, lane + 32, ...
+          for (int b = 0; b < mc; ++b) {
+            const float4 me = cpos[w][b];
+            for (unsigned i = lane; i < mn; i += 32) {
+              const int ent = pair_entry(a, me, tile[w][i], mol0);
+              if (ent != -1) {
+                const int q = atomicAdd(&scount[w][b], 1);
+                if (q < LIST_CAP) sent[w][b][q] = ent;
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane < mc) {
+          const int g = __float_as_int(cpos[w][lane].w) & JMASK;
+          const int total = scount[w][lane];
+          const int cnt = min(total, a.cap);
+          if (total > a.cap) fl |= B_EOVF;
+          int* e = sent[w][lane];
+          for (int x = 1; x < cnt; ++x) {     // order by partner slot: the force sum order is fixed
+            const int v = e[x];
+            int y = x;
+            while (y > 0 && (e[y - 1] & JMASK) > (v & JMASK)) { e[y] = e[y - 1]; --y; }
+            e[y] = v;
+          }
+          for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.n + g] = e[q];
+          a.ncnt[g] = cnt;
+        }
+        __syncwarp();
+      }
+    }
   }
 }
 
@@ -347,7 +618,7 @@ __device__ __forceinline__ void store_state(const KArgs<Real>& a, int nxt, int64
 template <class Real, int MODE>
 __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t base, int cur, int64_t step,
                              unsigned& fl, double* eacc) {
-  const int T = blockDim.x, tid = threadIdx.x;
+  const int T = SEG, tid = threadIdx.x & 31;
   const int nxt = cur ^ 1;
   // 1. stage slots base-4 .. base+T+3
   for (int s = tid; s < T + 8; s += T) {
@@ -359,7 +630,7 @@ __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int6
       sm.flg[s] = 0;
     }
   }
-  __syncthreads();
+  __syncwarp();
   // 2. bonded terms of owners base-2 .. base+T+1
   Real Eb[NTERMS];
   Real Wb[6];
@@ -375,7 +646,7 @@ __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int6
       owner_terms<Real>(a, sm, oi, fl, nullptr, nullptr);
     }
   }
-  __syncthreads();
+  __syncwarp();
   // 3. own nucleotide
   const int64_t g = base + tid;
   if (g < a.n) {
@@ -502,7 +773,12 @@ __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int6
         // App. A Eq. 8 per site: friction -gamma v_s and noise eta_s, summed over the dumbbell
         const V3<Real> eb = site_noise(a, local, step, mol, 0);
         const V3<Real> ep = site_noise(a, local, step, mol, 1);
-        const V3<Real> Vh{(Real)Vd[0], (Real)Vd[1], (Real)Vd[2]};
+        V3<Real> Vh;
+        if constexpr (sizeof(Real) == 4) {
+          Vh = V3<Real>{d2f_bits(Vd[0]), d2f_bits(Vd[1]), d2f_bits(Vd[2])};
+        } else {
+          Vh = V3<Real>{Vd[0], Vd[1], Vd[2]};
+        }
         Ft = F - a.c.gam2 * Vh + eb + ep;
         Tt = Tc - a.c.gamr * Om + h * cross(um, ep - eb);
       }
@@ -520,7 +796,11 @@ __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int6
         V3<Real> un = um;
         if (!frozen) {
           const V3<Real> dv = a.c.dtM * Ft;
-          Vd[0] += (double)dv.x; Vd[1] += (double)dv.y; Vd[2] += (double)dv.z;
+          if constexpr (sizeof(Real) == 4) {
+            Vd[0] += f2d_bits(dv.x); Vd[1] += f2d_bits(dv.y); Vd[2] += f2d_bits(dv.z);
+          } else {
+            Vd[0] += dv.x; Vd[1] += dv.y; Vd[2] += dv.z;
+          }
           Om += a.c.dtI * Tt;
           Om -= dot(Om, um) * um;
           Xd[0] = fma(a.c.dt_d, Vd[0], Xd[0]);
@@ -535,7 +815,7 @@ __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int6
             un = cs * um + sn * cross(ax, um);
             un = rsqrt_(dot(un, un)) * un;
           }
-          if (!(isfinite(Vd[0]) && isfinite(Vd[1]) && isfinite(Vd[2]) && isfinite(Om.x) && isfinite(Om.y) &&
+          if (!(isfinite(Ft.x) && isfinite(Ft.y) && isfinite(Ft.z) && isfinite(Om.x) && isfinite(Om.y) &&
                 isfinite(Om.z)))
             fl |= B_ENAN;
           a.V[g] = Vd[0]; a.V[a.n + g] = Vd[1]; a.V[2 * a.n + g] = Vd[2];
@@ -567,80 +847,90 @@ __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int6
     }
   }
   (void)eacc;
-  __syncthreads();
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- rebuild kernels
+// The neighbour-list rebuild runs as five ordinary kernels (full occupancy,
+// their own register budgets) between persistent step launches: bin + count,
+// block sums, scan, scatter to cell order, list build.
+template <class Real>
+__global__ void k_rebuild_bin(const KArgs<Real> a) {
+  unsigned fl = 0;
+  rebuild_bin(a, (int)(*a.step & 1), fl);
+  if (fl) atomicOr(a.err, fl & B_ERRMASK);
+}
+template <class Real>
+__global__ void k_rebuild_scan_a(const KArgs<Real> a) {
+  __shared__ unsigned s_red[32];
+  rebuild_scan_a(a, s_red);
+}
+template <class Real>
+__global__ void k_rebuild_scan_b(const KArgs<Real> a) {
+  __shared__ unsigned s_red[32];
+  rebuild_scan_b(a, s_red);
+}
+template <class Real>
+__global__ void k_rebuild_scatter(const KArgs<Real> a) { rebuild_scatter(a); }
+template <class Real, int CAPMAX>
+__global__ void __launch_bounds__(256) k_rebuild_list(const KArgs<Real> a) {
+  unsigned fl = 0;
+  rebuild_list_warps<Real, CAPMAX>(a, fl);
+  if (fl) atomicOr(a.err, fl & B_ERRMASK);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.rebuild = 0;
+    *a.nrebuild += 1;
+  }
 }
 
 // ---------------------------------------------------------------- persistent kernel
-template <class Real, int CAPMAX>
-__device__ bool do_rebuild(const KArgs<Real>& a, int cur, unsigned* s_word, unsigned* s_red) {
-  unsigned fl = 0;
-  rebuild_bin(a, cur, fl);
-  unsigned r = grid_sync(a.bar, gridDim.x, fl, a.spin_budget, s_word);
-  if (r & B_ERRMASK) return false;
-  rebuild_scan_a(a, s_red);
-  r = grid_sync(a.bar, gridDim.x, 0u, a.spin_budget, s_word);
-  if (r & B_ERRMASK) return false;
-  rebuild_scan_b(a, s_red);
-  r = grid_sync(a.bar, gridDim.x, 0u, a.spin_budget, s_word);
-  if (r & B_ERRMASK) return false;
-  rebuild_scatter(a);
-  r = grid_sync(a.bar, gridDim.x, 0u, a.spin_budget, s_word);
-  if (r & B_ERRMASK) return false;
-  fl = 0;
-  rebuild_list<Real, CAPMAX>(a, fl);
-  r = grid_sync(a.bar, gridDim.x, fl, a.spin_budget, s_word);
-  if (r & B_ERRMASK) return false;
-  return true;
-}
-
+// MODE_STEP: advance up to *steps_left steps (all of them when steps_left is
+// null: nsteps), one bounded grid barrier per step; stop early when a bead
+// moved more than skin/2 (the rebuild kernels run next) or on an error.
+// MODE_FORCES / MODE_ENERGY: one pass with the current list.
 template <class Real, int MODE, int CAPMAX>
-__global__ void engine_kernel(const KArgs<Real> a) {
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 1) engine_kernel(const KArgs<Real> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned s_word;
-  __shared__ unsigned s_red[32];
   __shared__ unsigned s_fl;
   const SegSmem<Real> sm = carve<Real>(smem_raw, blockDim.x);
   const int64_t step0 = *a.step;
-  int need = *a.rebuild;
+  int64_t budget = (MODE == MODE_STEP) ? (a.steps_left ? *a.steps_left : a.nsteps) : 1;
+  if (MODE == MODE_STEP && (*a.err & B_ERRMASK)) budget = 0;
+  int need = 0;
   int64_t done = 0;
-  unsigned long long builds = 0;
   unsigned errbits = 0;
-  const int64_t nsteps = (MODE == MODE_STEP) ? a.nsteps : 1;
-  for (int64_t it = 0; it < nsteps; ++it) {
+  for (int64_t it = 0; it < budget; ++it) {
     const int64_t step = step0 + it;
     const int cur = (int)(step & 1);
-    if (need) {
-      if (!do_rebuild<Real, CAPMAX>(a, cur, &s_word, s_red)) { errbits = s_word; break; }
-      need = 0;
-      ++builds;
-    }
     if (threadIdx.x == 0) s_fl = 0;
     __syncthreads();
     unsigned fl = 0;
-    for (int64_t seg = blockIdx.x; seg < a.nseg; seg += gridDim.x)
-      segment_pass<Real, MODE>(a, sm, seg * (int64_t)blockDim.x, cur, step, fl, nullptr);
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t seg = blockIdx.x * wpb + (threadIdx.x >> 5); seg < a.nseg; seg += gridDim.x * wpb)
+      segment_pass<Real, MODE>(a, sm, seg * (int64_t)SEG, cur, step, fl, nullptr);
     if (fl) atomicOr(&s_fl, fl);
     __syncthreads();
     if (MODE != MODE_STEP) {
       errbits = s_fl;
-      if (errbits) atomicOr(a.err, errbits & B_ERRMASK);
       break;
     }
     const unsigned r = grid_sync(a.bar, gridDim.x, s_fl, a.spin_budget, &s_word);
     if (r & B_ERRMASK) { errbits = r; break; }
-    need = (r & B_STALE) ? 1 : 0;
     ++done;
+    if (r & B_STALE) { need = 1; break; }
   }
   if (threadIdx.x == 0) {
     if (errbits & B_ERRMASK) atomicOr(a.err, errbits & B_ERRMASK);
-    if (blockIdx.x == 0) {
-      if (MODE == MODE_STEP) {
-        *a.step = step0 + done;
-        *a.rebuild = need;
-      } else {
-        *a.rebuild = 0;
+    if (blockIdx.x == 0 && MODE == MODE_STEP) {
+      *a.step = step0 + done;
+      if (need) *a.rebuild = 1;
+      const int64_t left = budget - done;
+      if (a.steps_left) *a.steps_left = left;
+      if (a.use_cond) {
+        const bool more = left > 0 && done > 0 && (errbits & B_ERRMASK) == 0;
+        cudaGraphSetConditional(a.h_while, more ? 1u : 0u);
       }
-      *a.nrebuild += builds;
     }
   }
 }

@@ -1,6 +1,8 @@
 // kern_launch.cuh -- host-side launch of the persistent engine kernel for one
 // precision; included once per precision by kern_mixed.cu / kern_fp64.cu.
 #pragma once
+#include <algorithm>
+
 #include "engine_kernels.cuh"
 
 namespace dsdna {
@@ -43,6 +45,26 @@ cudaError_t engine_launch(int mode, const KArgs<Real>& a, int grid, int T, size_
     case MODE_FORCES: return cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_FORCES, CAPMAX>, a);
     default: return cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_ENERGY, CAPMAX>, a);
   }
+}
+
+// The five rebuild kernels on stream st (grid-stride; the scan pair shares one grid).
+template <class Real>
+cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st) {
+  const int T = 256;
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (a.n + T - 1) / T;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 16));
+  k_rebuild_bin<Real><<<grid, T, 0, st>>>(a);
+  k_rebuild_scan_a<Real><<<scan_grid, T, 0, st>>>(a);
+  k_rebuild_scan_b<Real><<<scan_grid, T, 0, st>>>(a);
+  k_rebuild_scatter<Real><<<grid, T, 0, st>>>(a);
+  int lbps = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lbps, k_rebuild_list<Real, CAPMAX>, T, 0);
+  const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.H + 255) / 256, (int64_t)nsm * std::max(1, lbps)));
+  k_rebuild_list<Real, CAPMAX><<<lgrid, T, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace dsdna

@@ -21,6 +21,7 @@
 namespace dsdna {
 template <class Real> cudaError_t engine_occupancy(int mode, int T, int* blocks_per_sm, size_t* smem);
 template <class Real> cudaError_t engine_launch(int mode, const KArgs<Real>& a, int grid, int T, size_t smem, cudaStream_t st);
+template <class Real> cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st);
 __attribute__((visibility("hidden"))) void fill_coef_mixed(const dsdna_params& p, Coef<float>& c);
 }  // namespace dsdna
 
@@ -196,7 +197,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
 
   KArgs<float> a{};
   fill_coef_mixed(*p, a.c);
-  a.n = n; a.n_mol = n_mol; a.nseg = (n + NA_T - 1) / NA_T; a.cap = NA_CAP;
+  a.n = n; a.n_mol = n_mol; a.nseg = (n + 31) / 32; a.cap = NA_CAP;
   a.nsteps = 0; a.noise_mode = 0; a.seed_lo = 0; a.seed_hi = 0;
   a.spin_budget = 4000000000ull;
   a.X = reinterpret_cast<double*>(b + O_X);
@@ -222,6 +223,8 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
     a.L[k] = periodic ? p->box[k] : 0.0;
     a.Lf[k] = (float)a.L[k];
     a.cellh[k] = (float)(periodic ? p->box[k] / nc[k] : cellh);
+    a.invcellh[k] = 1.0f / a.cellh[k];
+    a.invLf[k] = periodic ? (float)(1.0 / a.L[k]) : 0.0f;
     a.Lfix[k] = (uint32_t)(uint64_t)llround(a.L[k] * 536870912.0);
   }
   a.mol_off = reinterpret_cast<int64_t*>(b + O_MOLOFF);
@@ -234,6 +237,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   a.nrebuild = reinterpret_cast<unsigned long long*>(ctrl + 8);
   a.fout = reinterpret_cast<double*>(b + O_FOUT);
   a.eout = nullptr;
+  a.steps_left = nullptr; a.use_cond = 0; a.h_while = 0;
 
   // the scratch keeps the previous call's contents: clear what must start at zero
   cudaError_t e = cudaMemcpyAsync(b + O_MOLOFF, mol_off, sizeof(int64_t) * (n_mol + 1), cudaMemcpyHostToDevice, st);
@@ -245,8 +249,10 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
                                                                const_cast<int*>(a.topo), ctrl);
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(s->grid, a.nseg));
-  e = engine_launch<float>(MODE_FORCES, a, grid, NA_T, s->smem, st);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(s->grid, (n + NA_T - 1) / NA_T));
+  const int scan_grid = (int)std::min<int64_t>(NA_MAX_GRID, std::max<int64_t>(1, ((int64_t)H + 2047) / 2048));
+  e = rebuild_launch<float>(a, scan_grid, st);
+  if (e == cudaSuccess) e = engine_launch<float>(MODE_FORCES, a, grid, NA_T, s->smem, st);
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
   k_noalloc_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.fout, n, F_bead, F_patch);
   e = cudaGetLastError();
