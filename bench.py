@@ -141,6 +141,53 @@ def run_cpu_oracle(cfg, steps: int, seconds_cap: float = 25.0):
     return cfg.n_nt * done / dt, done, dt
 
 
+def timed_steps(ctx, torch, steps, reps):
+    """Device time of reps x ctx.step(steps) after a warm-up, CUDA events on the context's stream."""
+    ctx.step(steps)
+    ctx.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.step(steps)
+    e1.record()
+    ctx.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def compare_batched(D, torch, n_mol=256, steps=100, fp64_sample=16, fp64_steps=50):
+    """Batched mixed-precision engine (256 ragged molecules, one graph-driven
+    persistent launch, autotuned) against the plain FP64 path that runs one
+    molecule per context, on the same molecules (FP64 timed on a sample)."""
+    from paper_1608_03722_gb300 import inputs as I
+    cfg = I.c4_batch(n_mol=n_mol, seed=0)
+    p = D.dsdna_default_params()
+    p, _ = D.dsdna_autotune(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether, trial_steps=30)
+    ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether)
+    for m in range(n_mol):
+        ctx.set_external_force_torque(m, cfg.ext_f[m], cfg.ext_t[m])
+    t = timed_steps(ctx, torch, steps, 3)
+    batched = cfg.n_nt * steps * 3 / t
+    ctx.close()
+    off = np.concatenate([[0], np.cumsum(cfg.n_bp)])
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(n_mol, size=fp64_sample, replace=False))
+    nt_steps, secs = 0, 0.0
+    for m in sample:
+        sl = slice(2 * off[m], 2 * off[m + 1])
+        pm = D.dsdna_default_params(precision=D.PREC_FP64)
+        c1 = D.Context(pm, [int(cfg.n_bp[m])], X=cfg.X[sl], V=cfg.V[sl], u=cfg.u[sl], Om=cfg.Om[sl], tether=[1])
+        c1.set_external_force_torque(0, cfg.ext_f[m], cfg.ext_t[m])
+        secs += timed_steps(c1, torch, fp64_steps, 1)
+        nt_steps += 2 * int(cfg.n_bp[m]) * fp64_steps
+        c1.close()
+    fp64 = nt_steps / secs
+    return {"workload": f"{n_mol} molecules log-uniform 500-20000 bp ({cfg.n_nt} nucleotides), own force and torque each",
+            "batched_mixed": {"value": batched, "unit": UNIT, "skin": p.skin, "block_threads": p.block_threads},
+            "fp64_per_molecule": {"value": fp64, "unit": UNIT, "sample_molecules": int(fp64_sample)},
+            "speedup": batched / fp64}
+
+
 def reference_arm(args, ws, rank):
     if rank != 0:
         return 0
@@ -173,6 +220,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the batched / FP64 per-molecule comparison")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     ws, rank, local = dist_env()
@@ -192,6 +241,11 @@ def main():
     cfg, desc = build_workload(args.workload, seed=rank, n_bp=args.n_bp)
     prec = D.PREC_MIXED if args.precision == "mixed" else D.PREC_FP64
     p = D.dsdna_default_params(precision=prec, box=cfg.box, seed=rank)
+    tuned = None
+    if not args.no_autotune:
+        p, ns = D.dsdna_autotune(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether, trial_steps=30)
+        tuned = {"skin": p.skin, "block_threads": p.block_threads, "blocks_per_sm": p.blocks_per_sm,
+                 "trial_ns_per_nt_step": ns}
     ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether)
     if cfg.ext_f is not None:
         for m in range(len(cfg.n_bp)):
@@ -229,7 +283,7 @@ def main():
 
     # neighbours per bead (full list), for the algorithmic byte count
     nbar = 2.0 * len(ctx.neighbor_pairs()) / cfg.n_nt
-    graph_chunk = ctx.info()["steps_per_graph"] if "steps_per_graph" in ctx.info() else 50
+    graph_chunk = ctx.params.steps_per_graph or 50
     launches_per_step = (S + graph_chunk - 1) // graph_chunk
     rebuilds = info1["rebuilds"] - info0["rebuilds"]
 
@@ -269,6 +323,10 @@ def main():
                "sample": f"{done} whole Langevin step(s) of the full workload ({cfg.n_nt} nucleotides), "
                          f"{dt:.1f} s, single thread"}
 
+    compare = None
+    if rank == 0 and not args.no_compare:
+        compare = compare_batched(D, torch)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
@@ -276,8 +334,9 @@ def main():
             "dtype": "f32+f64" if prec == D.PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": desc, "md_steps_per_step": S, "n_nucleotides": cfg.n_nt,
                        "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (state > 129 MB)",
-                       "rebuilds_in_timed_region": rebuilds, "graph_steps_per_launch": graph_chunk},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                       "rebuilds_in_timed_region": rebuilds, "graph_steps_per_launch": graph_chunk,
+                       "autotuned": tuned},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "compare": compare,
             "gpu_launches": K * launches_per_step, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

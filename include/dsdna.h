@@ -106,7 +106,7 @@ typedef struct dsdna_params {
   int noise;                             /* DSDNA_NOISE_* */
   int steric_phase;                      /* steric iff (index along strand from its 5' end) % 3 == phase */
   double box[3];                         /* > 0: periodic edge in that direction; <= 0: open */
-  double skin;                           /* neighbour-list skin (0: default 0.3) */
+  double skin;                           /* neighbour-list skin, at most 1 nm (0: default 0.3) */
   int precision;                         /* DSDNA_PREC_MIXED (FP32 forces, FP64 X/V) or DSDNA_PREC_FP64 */
   int max_neighbors;                     /* neighbour capacity per bead (0: default 32; at most 32) */
   int block_threads;                     /* nucleotides per CTA segment (0: default 256; 64..256, multiple of 32) */
@@ -221,6 +221,19 @@ const char* dsdna_last_error(const dsdna_ctx* ctx);
 
 /* Release every device buffer and the context. */
 void dsdna_destroy(dsdna_ctx* ctx);
+
+/* Autotuner for the engine's launch and list parameters (no counterpart in
+ * the paper, which ran LAMMPS with hand-set neighbour settings, Sec. 6).
+ * Runs trial_steps warm-up steps and trial_steps timed steps of the system
+ * sys on temporary contexts for every candidate neighbour skin
+ * (0.2 .. 0.6 nm), CTA size (128, 256) and persistent CTAs per SM, and writes
+ * to *best the copy of *base with the fastest choice (ns per
+ * nucleotide-step in *best_ns, may be NULL).  The candidates change how
+ * often the list is rebuilt and how work is spread, never the computed
+ * forces.  Allocates and frees through alloc like dsdna_create; synchronises
+ * cuda_stream.  Returns DSDNA_OK, DSDNA_EINVAL or DSDNA_ECUDA. */
+int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys, const dsdna_allocator* alloc, void* cuda_stream,
+                   int trial_steps, dsdna_params* best, double* best_ns);
 
 /* Force pass that allocates nothing.  The paper has no counterpart: this call
  * exists for callers that cannot call cudaMalloc, such as processes whose

@@ -331,7 +331,7 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
     return fail(nullptr, DSDNA_EINVAL, "non-positive dt/mass/ell/R0/rc or negative gamma/kT");
   if (p->precision != DSDNA_PREC_MIXED && p->precision != DSDNA_PREC_FP64) return fail(nullptr, DSDNA_EINVAL, "precision");
   if (p->noise < 0 || p->noise > 2) return fail(nullptr, DSDNA_EINVAL, "noise mode");
-  if (p->skin < 0.0) return fail(nullptr, DSDNA_EINVAL, "negative skin");
+  if (p->skin < 0.0 || p->skin > 1.0) return fail(nullptr, DSDNA_EINVAL, "skin must be in [0, 1] nm");
   if (p->max_neighbors < 0 || p->max_neighbors > 32) return fail(nullptr, DSDNA_EINVAL, "max_neighbors must be <= 32");
   if (p->block_threads && (p->block_threads < 64 || p->block_threads > 256 || p->block_threads % 32))
     return fail(nullptr, DSDNA_EINVAL, "block_threads must be a multiple of 32 in [64, 256]");
@@ -894,6 +894,55 @@ extern "C" int64_t dsdna_step_counter(const dsdna_ctx* c) { return c ? c->step :
 
 extern "C" const char* dsdna_last_error(const dsdna_ctx* c) {
   return c ? c->errmsg.c_str() : g_create_error.c_str();
+}
+
+// Autotuner: time short runs of each candidate (neighbour skin x CTA size x
+// persistent CTAs per SM) on temporary contexts of the same system and keep
+// the fastest.  Candidates never change the physics: the skin only sets how
+// often the list is rebuilt, the launch shape only how work is spread.
+extern "C" int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys, const dsdna_allocator* alloc,
+                              void* cuda_stream, int trial_steps, dsdna_params* best, double* best_ns) {
+  if (!base || !sys || !best || trial_steps < 1) return fail(nullptr, DSDNA_EINVAL, "autotune: bad arguments");
+  const double skins[] = {0.2, 0.3, 0.4, 0.5, 0.6};
+  const int blocks[] = {128, 256};
+  const int per_sm[] = {0, 2};
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(nullptr, DSDNA_ECUDA, "autotune: event creation failed");
+  double best_t = 1e300;
+  dsdna_params winner = *base;
+  int tried = 0;
+  std::string why;
+  for (double sk : skins)
+    for (int T : blocks)
+      for (int ps : per_sm) {
+        dsdna_params p = *base;
+        p.skin = sk;
+        p.block_threads = T;
+        p.blocks_per_sm = ps;
+        dsdna_ctx* c = nullptr;
+        if (dsdna_create(&p, sys, alloc, cuda_stream, &c) != DSDNA_OK) { why = g_create_error; continue; }
+        float ms = 0.f;
+        bool ok = dsdna_step(c, trial_steps) == DSDNA_OK && dsdna_synchronize(c) == DSDNA_OK;   // warm-up + first build
+        if (ok) {
+          ok = cudaEventRecord(e0, st) == cudaSuccess && dsdna_step(c, trial_steps) == DSDNA_OK &&
+               cudaEventRecord(e1, st) == cudaSuccess && dsdna_synchronize(c) == DSDNA_OK &&
+               cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        }
+        const double t = 1e6 * (double)ms / ((double)trial_steps * (double)c->n);   // ns per nucleotide-step
+        if (!ok) why = c->errmsg.empty() ? std::string("event timing failed") : c->errmsg;
+        dsdna_destroy(c);
+        if (!ok) continue;
+        ++tried;
+        if (t < best_t) { best_t = t; winner = p; }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!tried) return fail(nullptr, DSDNA_ECUDA, "autotune: no candidate ran (last: " + why + ")");
+  *best = winner;
+  if (best_ns) *best_ns = best_t;
+  return DSDNA_OK;
 }
 
 extern "C" void dsdna_destroy(dsdna_ctx* c) {

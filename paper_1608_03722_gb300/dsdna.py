@@ -62,7 +62,7 @@ class dsdna_info(C.Structure):
 EXPORTS = ["dsdna_default_params", "dsdna_create", "dsdna_set_external_force_torque", "dsdna_step",
            "dsdna_synchronize", "dsdna_energy_virial", "dsdna_observables", "dsdna_get_state", "dsdna_set_state",
            "dsdna_compute_forces", "dsdna_neighbor_pairs", "dsdna_get_info", "dsdna_step_counter",
-           "dsdna_last_error", "dsdna_destroy", "dsdna_forces_noalloc"]
+           "dsdna_last_error", "dsdna_destroy", "dsdna_forces_noalloc", "dsdna_autotune"]
 
 _lib = None
 
@@ -101,6 +101,9 @@ def load(build_if_missing: bool = True):
     L.dsdna_forces_noalloc.argtypes = [P(dsdna_params), C.c_int, P(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]
     L.dsdna_forces_noalloc.restype = C.c_int
+    L.dsdna_autotune.argtypes = [P(dsdna_params), P(dsdna_system), P(dsdna_allocator), C.c_void_p, C.c_int,
+                                 P(dsdna_params), P(C.c_double)]
+    L.dsdna_autotune.restype = C.c_int
     for name in EXPORTS:
         fn = getattr(L, name)
         if fn.restype is C.c_int or name in ("dsdna_create",):
@@ -199,6 +202,28 @@ def dsdna_create(params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, te
                         C.c_void_p(stream), C.byref(h))
     _check(None, rc)
     return h, alloc
+
+
+def dsdna_autotune(params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, tether=None, trial_steps=50,
+                   stream=None, allocator="torch"):
+    """Fastest (skin, CTA size, CTAs per SM) for this system; returns (params, ns per nucleotide-step)."""
+    L = load()
+    nb = np.ascontiguousarray(np.atleast_1d(n_bp), dtype=np.int32)
+    n = 2 * int(nb.sum())
+    X, V, u, Om = _f64(X, n), _f64(V, n), _f64(u, n), _f64(Om, n)
+    tt = None if tether is None else np.ascontiguousarray(np.atleast_1d(tether), dtype=np.int32)
+    sys = dsdna_system(len(nb), nb.ctypes.data_as(C.POINTER(C.c_int)), _dp(X), _dp(V), _dp(u), _dp(Om),
+                       None if tt is None else tt.ctypes.data_as(C.POINTER(C.c_int)))
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    alloc = _TorchAllocator(stream) if allocator == "torch" else None
+    best = dsdna_params()
+    ns = C.c_double()
+    rc = L.dsdna_autotune(C.byref(params), C.byref(sys), C.byref(alloc.struct) if alloc else None, C.c_void_p(stream),
+                          int(trial_steps), C.byref(best), C.byref(ns))
+    _check(None, rc)
+    return best, ns.value
 
 
 class Context:
