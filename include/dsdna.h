@@ -266,6 +266,39 @@ int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys, const dsdn
 int dsdna_forces_noalloc(const dsdna_params* params, int n_mol, const int* n_bp, const double* X, const double* u,
                          double* F_bead, double* F_patch, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Surrogate of the force/torque sweeps: an MLP 4 -> 64 -> 64 -> 3 with GELU
+ * activations (the paper has no surrogate; Sec. 4 runs one simulation per
+ * load).  Inputs per row: (force along z [kT/nm], end torque about z [kT],
+ * length [bp], kT); outputs: (mean extension / contour length, excess twist
+ * (Tw - Tw0)/Tw0, denatured-bp fraction).  Weights are FP32 masters with
+ * BF16 copies; every contraction runs on the tensor cores with BF16 operands
+ * and FP32 accumulation.  Parameters are packed FP32, row-major:
+ * W1[64][4] b1[64] W2[64][64] b2[64] W3[3][64] b3[3] (dsdna_mlp_num_params
+ * values).  Inputs are normalised inside the kernels with in_mean / in_scale
+ * and outputs produced as out_mean + out_scale * (network output).
+ * X, Y, T are DEVICE arrays of float ([B][4], [B][3], [B][3]); work runs on
+ * the network's stream. */
+typedef struct dsdna_mlp dsdna_mlp;
+
+/* Network for batches of up to max_batch rows; parameters start at zero. */
+int dsdna_mlp_create(int max_batch, const dsdna_allocator* alloc, void* cuda_stream, dsdna_mlp** out);
+int dsdna_mlp_num_params(void);
+/* Host arrays; any may be NULL (unchanged).  New parameters reset Adam. */
+int dsdna_mlp_set_params(dsdna_mlp* net, const float* params, const float* in_mean, const float* in_scale,
+                         const float* out_mean, const float* out_scale);
+/* Host copies of the FP32 parameters and of the last gradients (either may be NULL). */
+int dsdna_mlp_get_params(dsdna_mlp* net, float* params, float* grads);
+/* Y = network(X) for B rows; keeps the activations for dsdna_mlp_backward. */
+int dsdna_mlp_forward(dsdna_mlp* net, const float* X, int B, float* Y);
+/* Gradients of the mean squared error over the B x 3 normalised outputs of
+ * the last forward pass against targets T; writes the loss to *loss_host
+ * (may be NULL, then the call does not wait). */
+int dsdna_mlp_backward(dsdna_mlp* net, const float* T, int B, float* loss_host);
+/* One Adam step (bias-corrected) on the FP32 masters; refreshes the BF16 copies. */
+int dsdna_mlp_adam_step(dsdna_mlp* net, float lr, float beta1, float beta2, float eps);
+void dsdna_mlp_destroy(dsdna_mlp* net);
+
 #ifdef __cplusplus
 }
 #endif

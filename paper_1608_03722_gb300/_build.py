@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdsdna.so")
-SOURCES = ["capi.cu", "kern_mixed.cu", "kern_fp64.cu", "observables.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "kern_mixed.cu", "kern_fp64.cu", "observables.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

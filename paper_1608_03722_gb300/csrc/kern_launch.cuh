@@ -23,7 +23,8 @@ template <class Real>
 cudaError_t engine_occupancy(int mode, int T, int* blocks_per_sm, size_t* smem) {
   *smem = seg_smem_bytes<Real>(T);
   const void* fn = engine_fn<Real>(mode);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  // the attribute is per kernel, shared by every context: allow the largest CTA any context may use
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem_bytes<Real>(256));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, T, *smem);
 }

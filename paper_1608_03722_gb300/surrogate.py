@@ -1,0 +1,241 @@
+"""Sweep surrogate: an MLP that maps (force, torque, length, kT) to the mean
+extension / contour length, the excess twist (Tw - Tw0)/Tw0 and the
+denatured-bp fraction of a tethered molecule, trained on sweeps the engine
+itself simulates.
+
+The network runs in libdsdna.so (dsdna_mlp_*: BF16 tensor-core forward and
+backward, FP32 accumulation, Adam); this module only marshals arguments,
+holds an ensemble for query-by-committee selection, and drives the batched
+engine to produce labels.  The full simulation stays the fallback and the
+judge: ``Surrogate.predict`` returns the committee spread so that uncertain
+points can be sent to ``simulate_sweep``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import dsdna as D
+
+NI, NO = 4, 3
+KT_LEVELS = np.round(np.linspace(0.8, 1.4, 7), 3)   # kT is a per-context parameter: points are run at these levels
+
+
+def _lib():
+    L = D.load()
+    if not getattr(L, "_mlp_ready", False):
+        P = C.POINTER
+        L.dsdna_mlp_create.argtypes = [C.c_int, P(D.dsdna_allocator), C.c_void_p, P(C.c_void_p)]
+        L.dsdna_mlp_num_params.argtypes = []
+        L.dsdna_mlp_set_params.argtypes = [C.c_void_p] + [P(C.c_float)] * 5
+        L.dsdna_mlp_get_params.argtypes = [C.c_void_p, P(C.c_float), P(C.c_float)]
+        L.dsdna_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+        L.dsdna_mlp_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, P(C.c_float)]
+        L.dsdna_mlp_adam_step.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_float]
+        L.dsdna_mlp_destroy.argtypes = [C.c_void_p]
+        L.dsdna_mlp_destroy.restype = None
+        L._mlp_ready = True
+    return L
+
+
+def _fp(a):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class Mlp:
+    """One network on the device (dsdna_mlp)."""
+
+    def __init__(self, max_batch: int = 4096, stream=None):
+        import torch
+        self.torch = torch
+        self.L = _lib()
+        self.stream = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        self._alloc = D._TorchAllocator(self.stream)
+        self.h = C.c_void_p()
+        rc = self.L.dsdna_mlp_create(int(max_batch), C.byref(self._alloc.struct), C.c_void_p(self.stream), C.byref(self.h))
+        if rc != 0:
+            raise D.DsdnaError(rc, "dsdna_mlp_create failed")
+        self.np = self.L.dsdna_mlp_num_params()
+        self.max_batch = max_batch
+
+    def set_params(self, params=None, in_mean=None, in_scale=None, out_mean=None, out_scale=None):
+        keep = [_fp(x) for x in (params, in_mean, in_scale, out_mean, out_scale)]
+        rc = self.L.dsdna_mlp_set_params(self.h, *[None if k is None else k[1] for k in keep])
+        if rc != 0:
+            raise D.DsdnaError(rc, "dsdna_mlp_set_params failed")
+
+    def get_params(self):
+        p = np.zeros(self.np, np.float32); g = np.zeros(self.np, np.float32)
+        rc = self.L.dsdna_mlp_get_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float)),
+                                         g.ctypes.data_as(C.POINTER(C.c_float)))
+        if rc != 0:
+            raise D.DsdnaError(rc, "dsdna_mlp_get_params failed")
+        return p, g
+
+    def forward(self, X, Y):
+        """X, Y: CUDA float32 tensors [B, 4], [B, 3]."""
+        rc = self.L.dsdna_mlp_forward(self.h, C.c_void_p(X.data_ptr()), int(X.shape[0]), C.c_void_p(Y.data_ptr()))
+        if rc != 0:
+            raise D.DsdnaError(rc, "dsdna_mlp_forward failed")
+
+    def backward(self, T, want_loss=True):
+        loss = C.c_float()
+        rc = self.L.dsdna_mlp_backward(self.h, C.c_void_p(T.data_ptr()), int(T.shape[0]),
+                                       C.byref(loss) if want_loss else None)
+        if rc != 0:
+            raise D.DsdnaError(rc, "dsdna_mlp_backward failed")
+        return loss.value
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        rc = self.L.dsdna_mlp_adam_step(self.h, float(lr), float(beta1), float(beta2), float(eps))
+        if rc != 0:
+            raise D.DsdnaError(rc, "dsdna_mlp_adam_step failed")
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            self.L.dsdna_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def input_norm(X):
+    """Affine scaling of every input onto [-1, 1] over the training range."""
+    lo, hi = np.asarray(X).min(0), np.asarray(X).max(0)
+    return (lo + hi) / 2.0, np.maximum((hi - lo) / 2.0, 1e-6)
+
+
+def _he_init(seed):
+    """He-style initial parameters for W1[64][4] b1 W2[64][64] b2 W3[3][64] b3."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, math.sqrt(2.0 / NI), 64 * NI), np.zeros(64), rng.normal(0, math.sqrt(2.0 / 64), 64 * 64),
+             np.zeros(64), rng.normal(0, math.sqrt(1.0 / 64), NO * 64), np.zeros(NO)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+class Surrogate:
+    """Committee of networks (different initial weights and minibatch orders)."""
+
+    def __init__(self, n_models: int = 4, max_batch: int = 4096, seed: int = 0):
+        import torch
+        self.torch = torch
+        self.models = [Mlp(max_batch) for _ in range(n_models)]
+        self.seed = seed
+        self.norm = None
+
+    def fit(self, X, T, iters: int = 2000, batch: int = 256, lr: float = 3e-3):
+        """Adam on random minibatches for every member (learning rate decayed tenfold); final full-batch losses."""
+        torch = self.torch
+        X = np.asarray(X, np.float32); T = np.asarray(T, np.float32)
+        in_mean, in_scale = input_norm(X)
+        out_mean, out_scale = T.mean(0), np.maximum(T.std(0), 1e-4)
+        self.norm = (in_mean, in_scale, out_mean, out_scale)
+        Xd = torch.tensor(X, device="cuda"); Td = torch.tensor(T, device="cuda")
+        n = X.shape[0]
+        Yd = torch.empty((max(batch, n), NO), device="cuda")
+        losses = []
+        for k, m in enumerate(self.models):
+            m.set_params(_he_init(self.seed + k), in_mean, in_scale, out_mean, out_scale)
+            rng = np.random.default_rng(self.seed + 100 + k)
+            for it in range(iters):
+                idx = torch.tensor(rng.choice(n, size=min(batch, n), replace=False), device="cuda")
+                xb = Xd[idx].contiguous(); tb = Td[idx].contiguous()
+                m.forward(xb, Yd[: xb.shape[0]])
+                m.backward(tb, want_loss=False)
+                m.adam(lr * (0.1 ** (it / iters)))
+            m.forward(Xd, Yd[:n])
+            losses.append(m.backward(Td))
+        return losses
+
+    def predict(self, X):
+        """Committee mean and spread of the outputs, [B, 3] each."""
+        torch = self.torch
+        Xd = torch.tensor(np.ascontiguousarray(X, np.float32), device="cuda")
+        outs = []
+        for m in self.models:
+            Yd = torch.empty((Xd.shape[0], NO), device="cuda")
+            m.forward(Xd, Yd)
+            outs.append(Yd)
+        Y = torch.stack(outs).cpu().numpy()
+        return Y.mean(0), Y.std(0)
+
+    def select(self, candidates, k: int):
+        """Query by committee: the k candidates on which the members disagree most
+        (spread summed over outputs in units of each output's scale)."""
+        _, sd = self.predict(candidates)
+        score = (sd / self.norm[3]).sum(1)
+        return np.argsort(-score)[:k]
+
+    def close(self):
+        for m in self.models:
+            m.close()
+
+
+def sample_points(n: int, seed: int = 0, length=(500, 20000), force=(0.1, 10.0), torque=(-5.0, 5.0)):
+    """Sweep inputs: force and torque uniform, length log-uniform, kT on the run levels."""
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(*force, n)
+    g = rng.uniform(*torque, n)
+    L = np.exp(rng.uniform(math.log(length[0]), math.log(length[1]), n)).round()
+    kT = rng.choice(KT_LEVELS, n)
+    return np.stack([f, g, L, kT], 1)
+
+
+def simulate_sweep(points, steps: int = 4000, measure_from: int = 2000, every: int = 200, seed: int = 0,
+                   max_nt_per_context: int = 3_000_000):
+    """Full simulations of the sweep points with the batched engine.
+
+    Every point is one tethered molecule of its length (relaxed helix along
+    z, base pair 0 anchored) with force f e_z and torque Gamma e_z on its
+    last base pair; points of one kT level run together in one context
+    (chunked by size).  The labels are the averages over the samples taken
+    every ``every`` steps from ``measure_from`` on of: R_z / (0.34 (N-1)),
+    (Tw - Tw0) / Tw0 and the denatured fraction.
+    """
+    from . import inputs as I
+    pts = np.asarray(points, np.float64)
+    out = np.zeros((len(pts), NO))
+    order = np.argsort(pts[:, 3], kind="stable")
+    groups = []
+    for kT in np.unique(pts[:, 3]):
+        idx = [i for i in order if pts[i, 3] == kT]
+        cur, tot = [], 0
+        for i in idx:
+            nt = 2 * int(pts[i, 2])
+            if cur and tot + nt > max_nt_per_context:
+                groups.append((kT, cur)); cur, tot = [], 0
+            cur.append(i); tot += nt
+        if cur:
+            groups.append((kT, cur))
+    for gi, (kT, idx) in enumerate(groups):
+        lengths = [int(pts[i, 2]) for i in idx]
+        cfg = I.ragged_batch(lengths, seed=seed + gi)
+        p = D.dsdna_default_params(kT=float(kT), seed=seed + 1000 + gi)
+        ctx = D.Context(p, cfg.n_bp, X=cfg.X, u=cfg.u, tether=np.ones(len(idx), np.int32))
+        for m, i in enumerate(idx):
+            ctx.set_external_force_torque(m, [0.0, 0.0, pts[i, 0]], [0.0, 0.0, pts[i, 1]])
+        acc = np.zeros((len(idx), NO)); ns = 0
+        done = 0
+        while done < steps:
+            ctx.step(every)
+            done += every
+            if done >= measure_from:
+                for m in range(len(idx)):
+                    o = ctx.observables(m, D.OBS_EXT | D.OBS_DENAT | D.OBS_TW)
+                    N = lengths[m]
+                    acc[m, 0] += o["rz"] / (0.34 * max(N - 1, 1))
+                    acc[m, 1] += (o["tw"] - o["tw_ideal"]) / o["tw_ideal"] if o["tw_ideal"] else 0.0
+                    acc[m, 2] += o["denat"]
+                ns += 1
+        ctx.close()
+        out[idx] = acc / max(ns, 1)
+    return out

@@ -1,0 +1,118 @@
+"""Tensor-core MLP surrogate kernels against the FP64 reference, training, and the sweep workflow."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_1608_03722_gb300 import surrogate as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _norm():
+    return dict(in_mean=np.array([5.0, 0.0, 1e4, 1.1]), in_scale=np.array([5.0, 5.0, 1e4, 0.3]),
+                out_mean=np.array([0.8, 0.0, 0.02]), out_scale=np.array([0.1, 0.03, 0.02]))
+
+
+def _net(torch, p, norm):
+    net = S.Mlp(max_batch=512)
+    net.set_params(p, norm["in_mean"], norm["in_scale"], norm["out_mean"], norm["out_scale"])
+    return net
+
+
+def _reference_params(p):
+    """The kernels multiply by BF16 copies of the weights; biases stay FP32."""
+    d = M.unpack(p)
+    for k in ("W1", "W2", "W3"):
+        d[k] = M.bf16(d[k])
+    return M.pack(d)
+
+
+@pytest.mark.parametrize("B", [1, 16, 70, 333])
+def test_forward_matches_fp64_reference(torch, B):
+    rng = np.random.default_rng(B)
+    p = (M.init_params(7) + rng.normal(0, 0.05, M.NP)).astype(np.float32)
+    X = np.stack([rng.uniform(0.1, 10, B), rng.uniform(-5, 5, B), rng.uniform(500, 2e4, B), rng.uniform(0.8, 1.4, B)], 1)
+    n = _norm()
+    net = _net(torch, p, n)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Yd = torch.empty((B, 3), device="cuda")
+    net.forward(Xd, Yd)
+    Y = Yd.cpu().numpy().astype(np.float64)
+    Yo, _ = M.forward(_reference_params(p.astype(np.float64)), X.astype(np.float32).astype(np.float64), n)
+    # BF16 operands (2^-9 relative) through three layers: a few 1e-3 of the output scale
+    err = np.abs(Y - Yo) / n["out_scale"]
+    assert err.max() < 3e-2, err.max()
+    net.close()
+
+
+def test_backward_matches_fp64_reference(torch):
+    rng = np.random.default_rng(5)
+    B = 300
+    p = (M.init_params(11) + rng.normal(0, 0.05, M.NP)).astype(np.float32)
+    X = np.stack([rng.uniform(0.1, 10, B), rng.uniform(-5, 5, B), rng.uniform(500, 2e4, B), rng.uniform(0.8, 1.4, B)], 1)
+    n = _norm()
+    T = n["out_mean"] + n["out_scale"] * rng.normal(0, 1, (B, 3))
+    net = _net(torch, p, n)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    Yd = torch.empty((B, 3), device="cuda")
+    net.forward(Xd, Yd)
+    loss = net.backward(Td)
+    _, g = net.get_params()
+    lo, go = M.loss_and_grad(_reference_params(p.astype(np.float64)), X.astype(np.float32).astype(np.float64),
+                             T.astype(np.float32).astype(np.float64), n)
+    assert abs(loss - lo) < 2e-2 * lo
+    gd, god = M.unpack(g.astype(np.float64)), M.unpack(go)
+    for name, _ in M.SHAPES:          # each block within a few BF16 roundings of the FP64 gradient
+        rel = np.linalg.norm(gd[name] - god[name]) / max(np.linalg.norm(god[name]), 1e-12)
+        assert rel < 3e-2, (name, rel)
+    net.close()
+
+
+def test_training_reduces_the_loss_on_a_smooth_function(torch):
+    rng = np.random.default_rng(3)
+    N = 1500
+    X = np.stack([rng.uniform(0.1, 10, N), rng.uniform(-5, 5, N), rng.uniform(500, 2e4, N), rng.uniform(0.8, 1.4, N)], 1)
+    T = np.stack([1.0 - 0.5 / np.sqrt(X[:, 0] + 0.5), 0.01 * X[:, 1] * X[:, 3], 0.05 * np.exp(-X[:, 0] / 3)], 1)
+    sur = S.Surrogate(n_models=2, max_batch=2048, seed=1)
+    losses = sur.fit(X[:1200], T[:1200], iters=1500, batch=256, lr=3e-3)
+    assert max(losses) < 0.02      # normalised MSE: from about 1 at the start
+    Y, sd = sur.predict(X[1200:])
+    r2 = 1 - ((Y - T[1200:]) ** 2).sum(0) / ((T[1200:] - T[1200:].mean(0)) ** 2).sum(0)
+    assert (r2 > 0.95).all(), r2
+    sur.close()
+
+
+def test_surrogate_sweep_gains_over_full_simulation(torch):
+    """Surrogate on sweeps the engine itself simulates: on held-out points it
+    reproduces the simulated excess twist (linear in the applied torque) and
+    the extension trend, at a small fraction of the simulation cost; the
+    committee spread points at where to simulate next."""
+    train = S.sample_points(224, seed=1, length=(40, 160))
+    test = S.sample_points(32, seed=2, length=(40, 160))
+    Ttrain = S.simulate_sweep(train, steps=4000, measure_from=1000, every=100, seed=1)
+    t1 = time.perf_counter()
+    Ttest = S.simulate_sweep(test, steps=4000, measure_from=1000, every=100, seed=2)
+    t_sim = time.perf_counter() - t1
+    assert np.isfinite(Ttrain).all() and np.isfinite(Ttest).all()
+    sur = S.Surrogate(n_models=4, max_batch=1024, seed=2)
+    sur.fit(train, Ttrain, iters=1200, batch=64, lr=3e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    Y, sd = sur.predict(test)
+    t_pred = time.perf_counter() - t2
+    r2 = 1 - ((Y - Ttest) ** 2).sum(0) / ((Ttest - Ttest.mean(0)) ** 2).sum(0)
+    assert r2[1] > 0.6, r2          # excess twist follows the torque (labels carry sampling noise)
+    assert t_pred < 0.05 * t_sim, (t_pred, t_sim)
+    pick = sur.select(S.sample_points(500, seed=3, length=(40, 160)), 20)
+    assert len(set(pick.tolist())) == 20
+    sur.close()
