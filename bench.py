@@ -59,6 +59,30 @@ def build_workload(name: str, seed: int = 0, n_bp: int = 1_000_000):
     return cfg, desc
 
 
+# DRAM bytes (read + write) per nucleotide-step of the mixed-precision step
+# kernel from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
+# one-step launches on the 500 kbp confined workload), keyed by a hash of the
+# kernel sources it was taken on: a changed kernel reports no traffic.
+ENGINE_TRAFFIC = {}
+ENGINE_SOURCES = ("engine.cuh", "engine_kernels.cuh", "kern_launch.cuh", "kern_mixed.cu")
+
+
+def engine_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ENGINE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1608_03722_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def engine_traffic_per_nt_step(prec):
+    from paper_1608_03722_gb300 import dsdna as D
+    if prec != D.PREC_MIXED:
+        return None
+    return ENGINE_TRAFFIC.get(engine_source_hash())
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -221,6 +245,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--skin", type=float, default=None, help="fixed skin (skips the autotuner)")
+    ap.add_argument("--block-threads", type=int, default=None, help="fixed CTA size (skips the autotuner)")
     ap.add_argument("--no-compare", action="store_true", help="skip the batched / FP64 per-molecule comparison")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
@@ -242,6 +268,12 @@ def main():
     prec = D.PREC_MIXED if args.precision == "mixed" else D.PREC_FP64
     p = D.dsdna_default_params(precision=prec, box=cfg.box, seed=rank)
     tuned = None
+    if args.skin is not None or args.block_threads is not None:
+        args.no_autotune = True
+        if args.skin is not None:
+            p.skin = args.skin
+        if args.block_threads is not None:
+            p.block_threads = args.block_threads
     if not args.no_autotune:
         p, ns = D.dsdna_autotune(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether, trial_steps=30)
         tuned = {"skin": p.skin, "block_threads": p.block_threads, "blocks_per_sm": p.blocks_per_sm,
@@ -281,11 +313,24 @@ def main():
     nt_steps = cfg.n_nt * S * K * ws
     value = nt_steps / (ms_max * 1e-3)
 
+    graph_chunk = ctx.params.steps_per_graph or 50
+    graph_launches = K * ((S + graph_chunk - 1) // graph_chunk)
+    rebuilds = info1["rebuilds"] - info0["rebuilds"]
+    engine_launches = info1["engine_launches"] - info0["engine_launches"]
+    # kernels of the timed region: per graph launch one loop-init kernel; per loop
+    # iteration one loop-head kernel and one persistent step kernel; five per rebuild
+    gpu_launches = graph_launches + 2 * engine_launches + 5 * rebuilds
+
+    # Roofline of the dominant kernel: K x S further steps queued launch by launch
+    # (dsdna_step_profiled), each step-kernel launch bracketed by CUDA events on
+    # the context stream.
+    prof = {"steps": 0, "engine_launches": 0, "engine_ms": 0.0, "rebuild_launches": 0, "rebuild_ms": 0.0}
+    for _ in range(K):
+        pr = ctx.step_profiled(S)
+        for k in prof:
+            prof[k] += pr[k]
     # neighbours per bead (full list), for the algorithmic byte count
     nbar = 2.0 * len(ctx.neighbor_pairs()) / cfg.n_nt
-    graph_chunk = ctx.params.steps_per_graph or 50
-    launches_per_step = (S + graph_chunk - 1) // graph_chunk
-    rebuilds = info1["rebuilds"] - info0["rebuilds"]
 
     # algorithmic bytes per nucleotide-step of the fused force + Langevin kernel:
     # state X,V (FP64) + u, Omega (FP32) read and written, position mirror read and written,
@@ -293,12 +338,21 @@ def main():
     state = 48 + 24 if prec == D.PREC_MIXED else 96
     mirror = 32 if prec == D.PREC_MIXED else 48
     b_nt = 2 * state + 2 * mirror + 4 + 4 + 4 * nbar
-    per_launch_bytes = b_nt * cfg.n_nt * graph_chunk
-    launch_s = ms_max * 1e-3 / (K * launches_per_step)
+    steps_per_launch = prof["steps"] / max(prof["engine_launches"], 1)
+    per_launch_bytes = b_nt * cfg.n_nt * steps_per_launch
+    launch_s = prof["engine_ms"] * 1e-3 / max(prof["engine_launches"], 1)
     hbm, peak_kind = peaks()
     achieved = per_launch_bytes / launch_s / 1e9
+    traffic = engine_traffic_per_nt_step(prec)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "peak_kind": peak_kind, "bytes_per_nt_step": b_nt, "neighbors_per_bead": nbar,
+            "traffic": None if traffic is None else traffic * cfg.n_nt * steps_per_launch,
+            "peak_kind": peak_kind, "bytes_per_nt_step": b_nt, "neighbors_per_bead": nbar,
+            "algorithmic_bytes_per_launch": per_launch_bytes, "steps_per_launch": steps_per_launch,
+            "launch_ms": launch_s * 1e3, "launches_timed": prof["engine_launches"],
+            "rebuild_ms_per_rebuild": prof["rebuild_ms"] / max(prof["rebuild_launches"], 1),
+            "share_of_step_time": prof["engine_ms"] / max(prof["engine_ms"] + prof["rebuild_ms"], 1e-30),
+            "timing": "CUDA events around every step-kernel launch on the context stream, "
+                      "K x md_steps steps run right after the timed region",
             "kernel": "engine_kernel<float,STEP> (fused forces + Langevin, persistent cooperative)"}
 
     # end to end through the C ABI with host buffers: upload state, step, download state
@@ -326,6 +380,17 @@ def main():
     compare = None
     if rank == 0 and not args.no_compare:
         compare = compare_batched(D, torch)
+        from paper_1608_03722_gb300 import surrogate as SUR
+        st = SUR.run_sweep_study(n_train=256, n_test=64, n_query=32, length=(500, 2000), steps=2000,
+                                 measure_from=500, every=100, iters=1500)
+        compare["surrogate"] = {
+            "workload": "sweep of tethered molecules 500-2000 bp, force 0.1-10 kT/nm, torque -5..5 kT, kT 0.8-1.4 "
+                        "(256 training / 64 held-out points, 2000 steps each)",
+            "held_out_r2": st["held_out"]["r2"], "held_out_rmse": st["held_out"]["rmse"],
+            "simulation_s_per_point": st["simulation_s_per_point"],
+            "surrogate_s_per_point": st["surrogate_s_per_point"], "speedup_per_point": st["speedup_per_point"],
+            "r2_after_committee_queries": st["after_committee_queries"]["r2"],
+            "r2_after_random_queries": st["after_random_queries"]["r2"]}
 
     if rank == 0:
         line = {
@@ -337,7 +402,7 @@ def main():
                        "rebuilds_in_timed_region": rebuilds, "graph_steps_per_launch": graph_chunk,
                        "autotuned": tuned},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "compare": compare,
-            "gpu_launches": K * launches_per_step, "clocks": clocks,
+            "gpu_launches": gpu_launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -45,8 +45,10 @@
  * non-finite force, list overflow, barrier timeout) is reported by the next
  * call that synchronises (dsdna_synchronize, get_state, energy_virial,
  * observables, compute_forces).  After any error the context is poisoned:
- * every call except set_state, last_error and destroy returns DSDNA_ESTATE
- * until dsdna_set_state installs a new state.  The device never traps.
+ * every call except get_state, set_state, last_error and destroy returns
+ * DSDNA_ESTATE until dsdna_set_state installs a new state.  get_state on a
+ * poisoned context returns the state at the step that raised the error.
+ * The device never traps.
  */
 #ifndef DSDNA_H
 #define DSDNA_H
@@ -158,7 +160,17 @@ typedef struct dsdna_info {
   double skin;
   int64_t cell_table;    /* entries of the cell hash table */
   int64_t device_bytes;  /* bytes allocated on the device */
+  int64_t engine_launches; /* persistent step/force/energy kernel launches so far */
 } dsdna_info;
+
+/* Per-launch timing of dsdna_step_profiled (CUDA events on the context stream). */
+typedef struct dsdna_prof {
+  int64_t steps;            /* steps advanced */
+  int64_t engine_launches;  /* persistent step-kernel launches */
+  double engine_ms;         /* summed event time of those launches */
+  int64_t rebuild_launches; /* neighbour-list rebuilds (five kernels each) */
+  double rebuild_ms;        /* summed event time of the rebuilds */
+} dsdna_prof;
 
 typedef struct dsdna_ctx dsdna_ctx;
 
@@ -184,6 +196,13 @@ int dsdna_step(dsdna_ctx* ctx, int64_t nsteps);
 /* Wait for queued work; returns the first device-side error, if any. */
 int dsdna_synchronize(dsdna_ctx* ctx);
 
+/* Advance nsteps like dsdna_step, but queue every rebuild and step-kernel
+ * launch from the host (no graph) and time each with a CUDA event pair on
+ * the context stream; the sums go to *out.  Same trajectory as dsdna_step
+ * (the kernels and the order of the steps are the same); slower by the host
+ * round trip after every launch.  Synchronises; returns device errors. */
+int dsdna_step_profiled(dsdna_ctx* ctx, int64_t nsteps, dsdna_prof* out);
+
 /* Energy per term (DSDNA_E_*) and site virial W = sum (r_s - r_ref) (x) F_s
  * (xx yy zz xy xz yz) of molecule mol (-1: sum over all), FP64 reductions.
  * Kinetic terms use the full-step velocities of the current step. */
@@ -194,7 +213,8 @@ int dsdna_energy_virial(dsdna_ctx* ctx, int mol, double energy[DSDNA_NTERMS], do
 int dsdna_observables(dsdna_ctx* ctx, int mol, unsigned flags, dsdna_obs* out);
 
 /* Copy the state of molecule mol (-1: all) to caller-owned host arrays
- * [3*n] each (any may be NULL).  Synchronises. */
+ * [3*n] each (any may be NULL).  Synchronises.  Also allowed on a poisoned
+ * context (post-mortem: the state at the step that raised the error). */
 int dsdna_get_state(dsdna_ctx* ctx, int mol, double* X, double* V, double* u, double* Om);
 
 /* Install a new state for molecule mol (-1: all) from host arrays (NULL

@@ -57,6 +57,9 @@ struct dsdna_ctx {
   double* fout = nullptr; double* eout = nullptr; double* stage = nullptr;
   double* obs_scratch = nullptr; double* obs_out = nullptr;
   int64_t* steps_left = nullptr; unsigned* iters = nullptr;
+  unsigned long long* nlaunch = nullptr;   // engine launches made by step graphs
+  int64_t host_launches = 0;               // engine launches queued directly by the host
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   unsigned H = 0;
   int morton_bits = 0;
   int nc[3] = {0, 0, 0};
@@ -452,6 +455,7 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   ALLOC(obs_out, double, 8);
   ALLOC(steps_left, int64_t, 1);
   ALLOC(iters, unsigned, 4);
+  ALLOC(nlaunch, unsigned long long, 1);
 #undef ALLOC
   // launch shape per mode (cooperative: every CTA resident)
   int nsm = 0;
@@ -492,6 +496,7 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
     return bad(fail(c, DSDNA_ECUDA, "topology upload"));
   if (cudaMemset(c->cnt, 0, sizeof(unsigned) * c->H) != cudaSuccess || cudaMemset(c->err, 0, 16) != cudaSuccess ||
       cudaMemset(c->step_d, 0, 8) != cudaSuccess || cudaMemset(c->nrebuild, 0, 8) != cudaSuccess ||
+      cudaMemset(c->nlaunch, 0, 8) != cudaSuccess ||
       cudaMemset(c->bar, 0, sizeof(GridBar)) != cudaSuccess || cudaMemset(c->ncnt, 0, sizeof(int) * nn) != cudaSuccess ||
       cudaMemset(c->Om, 0, (f64 ? 8 : 4) * 3 * nn) != cudaSuccess || cudaMemset(c->V, 0, 24 * nn) != cudaSuccess)
     return bad(fail(c, DSDNA_ECUDA, "initialisation"));
@@ -535,8 +540,10 @@ __global__ void k_loop_init(int64_t* steps_left, int64_t nsteps, unsigned* iters
 // step kernel that never runs ends it); more iterations than steps means no
 // progress and ends the loop with a timeout error.
 __global__ void k_loop_head(const int* rebuild, unsigned* iters, unsigned max_iters, unsigned* err, int64_t* steps_left,
-                            cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_if) {
+                            unsigned long long* nlaunch, cudaGraphConditionalHandle h_while,
+                            cudaGraphConditionalHandle h_if) {
   const unsigned it = ++*iters;
+  ++*nlaunch;                       // every iteration runs one step kernel
   cudaGraphSetConditional(h_while, 0u);
   bool ok = (*err & B_ERRMASK) == 0;
   if (it > max_iters) {
@@ -552,9 +559,11 @@ static cudaError_t launch_rebuild(dsdna_ctx* c) {
 }
 
 static cudaError_t launch_engine(dsdna_ctx* c, int mode, int64_t nsteps, int64_t* steps_left, int use_cond,
-                                 cudaGraphConditionalHandle hw) {
+                                 cudaGraphConditionalHandle hw, cudaEvent_t ev_start = nullptr) {
   cudaError_t e = cudaMemsetAsync(c->bar, 0, sizeof(GridBar), c->st);
   if (e != cudaSuccess) return e;
+  if (ev_start && (e = cudaEventRecord(ev_start, c->st)) != cudaSuccess) return e;
+  if (!use_cond) ++c->host_launches;
   if (c->fp64()) {
     KArgs<double> a = c->kd;
     a.nsteps = nsteps; a.steps_left = steps_left; a.use_cond = use_cond; a.h_while = hw;
@@ -609,7 +618,8 @@ static cudaError_t build_step_graph(dsdna_ctx* c, int64_t K, cudaGraphExec_t* ou
     unsigned maxit = (unsigned)(K + 2);
     unsigned* er = c->err;
     int64_t* sl = c->steps_left;
-    void* args[] = {&rb, &it, &maxit, &er, &sl, &hw, &hi};
+    unsigned long long* nl = c->nlaunch;
+    void* args[] = {&rb, &it, &maxit, &er, &sl, &nl, &hw, &hi};
     cudaKernelNodeParams kp = {};
     kp.func = (void*)k_loop_head;
     kp.gridDim = dim3(1);
@@ -729,6 +739,49 @@ extern "C" int dsdna_step(dsdna_ctx* c, int64_t nsteps) {
   return DSDNA_OK;
 }
 
+// Host-driven steps with a CUDA event pair around every rebuild and every
+// step-kernel launch on the context stream.
+extern "C" int dsdna_step_profiled(dsdna_ctx* c, int64_t nsteps, dsdna_prof* out) {
+  if (!c || !out) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  if (nsteps < 0) return fail(c, DSDNA_EINVAL, "negative step count");
+  std::memset(out, 0, sizeof(*out));
+  for (int k = 0; k < 4; ++k)
+    if (!c->ev[k]) CK(cudaEventCreate(&c->ev[k]), "event create");
+  int64_t dstep = 0;
+  CK(cudaStreamSynchronize(c->st), "step sync");
+  CK(cudaMemcpy(&dstep, c->step_d, sizeof(dstep), cudaMemcpyDeviceToHost), "read step");
+  const int64_t first = dstep, target = dstep + nsteps;
+  for (int64_t guard = 0; guard < nsteps + 2 && dstep < target; ++guard) {
+    int rb = 0;
+    unsigned er = 0;
+    CK(cudaMemcpy(&rb, c->rebuild, sizeof(rb), cudaMemcpyDeviceToHost), "read rebuild flag");
+    CK(cudaMemcpy(&er, c->err, sizeof(er), cudaMemcpyDeviceToHost), "read error word");
+    if (er) break;
+    if (rb) {
+      CK(cudaEventRecord(c->ev[0], c->st), "event record");
+      CK(launch_rebuild(c), "rebuild launch");
+      CK(cudaEventRecord(c->ev[1], c->st), "event record");
+    }
+    CK(launch_engine(c, MODE_STEP, target - dstep, nullptr, 0, 0, c->ev[2]), "engine launch");
+    CK(cudaEventRecord(c->ev[3], c->st), "event record");
+    CK(cudaStreamSynchronize(c->st), "step sync");
+    float ms = 0.f;
+    if (rb) {
+      CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]), "event time");
+      out->rebuild_ms += ms;
+      ++out->rebuild_launches;
+    }
+    CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]), "event time");
+    out->engine_ms += ms;
+    ++out->engine_launches;
+    CK(cudaMemcpy(&dstep, c->step_d, sizeof(dstep), cudaMemcpyDeviceToHost), "read step");
+  }
+  out->steps = dstep - first;
+  c->step += out->steps;
+  return sync_check(c);
+}
+
 extern "C" int dsdna_synchronize(dsdna_ctx* c) {
   if (!c) return DSDNA_EINVAL;
   if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
@@ -791,10 +844,15 @@ extern "C" int dsdna_observables(dsdna_ctx* c, int mol, unsigned flags, dsdna_ob
 
 extern "C" int dsdna_get_state(dsdna_ctx* c, int mol, double* X, double* V, double* u, double* Om) {
   if (!c) return DSDNA_EINVAL;
-  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
   if (mol < -1 || mol >= c->n_mol) return fail(c, DSDNA_EINVAL, "molecule index out of range");
-  int rc = sync_check(c);
-  if (rc) return rc;
+  if (c->poisoned) {
+    // Post-mortem read: the engine stopped at the step that raised the error,
+    // so the state shows it; the error itself stays in last_error.
+    CK(cudaStreamSynchronize(c->st), "synchronize");
+  } else {
+    int rc = sync_check(c);
+    if (rc) return rc;
+  }
   const int64_t g0 = mol < 0 ? 0 : 2 * c->off[mol];
   const int64_t cnt = mol < 0 ? c->n : 2 * (int64_t)c->n_bp[mol];
   const int cur = (int)(c->step & 1);
@@ -880,6 +938,8 @@ extern "C" int dsdna_get_info(const dsdna_ctx* c, dsdna_info* info) {
   cudaStreamSynchronize(c->st);
   cudaMemcpy(&nb, c->nrebuild, sizeof(nb), cudaMemcpyDeviceToHost);
   info->rebuilds = (int64_t)nb;
+  cudaMemcpy(&nb, c->nlaunch, sizeof(nb), cudaMemcpyDeviceToHost);
+  info->engine_launches = (int64_t)nb + c->host_launches;
   info->grid_blocks = c->grid[MODE_STEP];
   info->block_threads = c->T;
   info->max_neighbors = c->p.max_neighbors;
@@ -948,6 +1008,8 @@ extern "C" int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys,
 extern "C" void dsdna_destroy(dsdna_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
+  for (cudaEvent_t& e : c->ev)
+    if (e) { cudaEventDestroy(e); e = nullptr; }
   free_all(c);
   delete c;
 }

@@ -56,11 +56,16 @@ class dsdna_info(C.Structure):
     _fields_ = [("n_nt", C.c_int64), ("n_mol", C.c_int), ("step", C.c_int64), ("rebuilds", C.c_int64),
                 ("grid_blocks", C.c_int), ("block_threads", C.c_int), ("max_neighbors", C.c_int),
                 ("precision", C.c_int), ("skin", C.c_double), ("cell_table", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("engine_launches", C.c_int64)]
+
+
+class dsdna_prof(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("engine_launches", C.c_int64), ("engine_ms", C.c_double),
+                ("rebuild_launches", C.c_int64), ("rebuild_ms", C.c_double)]
 
 
 EXPORTS = ["dsdna_default_params", "dsdna_create", "dsdna_set_external_force_torque", "dsdna_step",
-           "dsdna_synchronize", "dsdna_energy_virial", "dsdna_observables", "dsdna_get_state", "dsdna_set_state",
+           "dsdna_step_profiled", "dsdna_synchronize", "dsdna_energy_virial", "dsdna_observables", "dsdna_get_state", "dsdna_set_state",
            "dsdna_compute_forces", "dsdna_neighbor_pairs", "dsdna_get_info", "dsdna_step_counter",
            "dsdna_last_error", "dsdna_destroy", "dsdna_forces_noalloc", "dsdna_autotune"]
 
@@ -84,6 +89,7 @@ def load(build_if_missing: bool = True):
     L.dsdna_create.argtypes = [P(dsdna_params), P(dsdna_system), P(dsdna_allocator), C.c_void_p, P(C.c_void_p)]
     L.dsdna_set_external_force_torque.argtypes = [C.c_void_p, C.c_int, d, d]
     L.dsdna_step.argtypes = [C.c_void_p, C.c_int64]
+    L.dsdna_step_profiled.argtypes = [C.c_void_p, C.c_int64, P(dsdna_prof)]
     L.dsdna_synchronize.argtypes = [C.c_void_p]
     L.dsdna_energy_virial.argtypes = [C.c_void_p, C.c_int, d, d]
     L.dsdna_observables.argtypes = [C.c_void_p, C.c_int, C.c_uint, P(dsdna_obs)]
@@ -247,6 +253,12 @@ class Context:
 
     def step(self, nsteps):
         _check(self.h, self.lib.dsdna_step(self.h, int(nsteps)))
+
+    def step_profiled(self, nsteps):
+        """dsdna_step_profiled: same steps, every launch timed with CUDA events."""
+        pr = dsdna_prof()
+        _check(self.h, self.lib.dsdna_step_profiled(self.h, int(nsteps), C.byref(pr)))
+        return {k: getattr(pr, k) for k, _ in dsdna_prof._fields_}
 
     def synchronize(self):
         _check(self.h, self.lib.dsdna_synchronize(self.h))

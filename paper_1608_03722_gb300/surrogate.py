@@ -136,6 +136,8 @@ class Surrogate:
         """Adam on random minibatches for every member (learning rate decayed tenfold); final full-batch losses."""
         torch = self.torch
         X = np.asarray(X, np.float32); T = np.asarray(T, np.float32)
+        ok = np.isfinite(T).all(1)          # points whose simulation broke carry NaN labels
+        X, T = X[ok], T[ok]
         in_mean, in_scale = input_norm(X)
         out_mean, out_scale = T.mean(0), np.maximum(T.std(0), 1e-4)
         self.norm = (in_mean, in_scale, out_mean, out_scale)
@@ -190,6 +192,66 @@ def sample_points(n: int, seed: int = 0, length=(500, 20000), force=(0.1, 10.0),
     return np.stack([f, g, L, kT], 1)
 
 
+def sweep_dt(kT: float) -> float:
+    """Timestep of a sweep run at temperature kT: 0.005 tau_Br with the
+    Brownian time tau_Br = gamma sigma^2 / kT of the run (App. A units), so
+    the step is 0.005 at kT = 1 and shrinks as the noise grows."""
+    return 0.005 / float(kT)
+
+
+def _broken_molecules(ctx, lengths, R0):
+    """Molecules whose post-mortem state holds a backbone bond at or beyond
+    0.98 R0 or a non-finite coordinate."""
+    X, V, u, Om = ctx.get_state()
+    off = np.concatenate([[0], np.cumsum(lengths)]) * 2
+    bad = []
+    for m in range(len(lengths)):
+        Xm, um = X[off[m]:off[m + 1]], u[off[m]:off[m + 1]]
+        if not (np.isfinite(Xm).all() and np.isfinite(V[off[m]:off[m + 1]]).all()):
+            bad.append(m)
+            continue
+        b = Xm - 0.25 * um
+        if len(b) > 2 and np.linalg.norm(b[2:] - b[:-2], axis=1).max() >= 0.98 * R0:
+            bad.append(m)
+    return bad
+
+
+def _run_group(lengths, loads, kT, seed, steps, measure_from, every):
+    """One context of tethered molecules at one kT; returns (labels, None) or
+    (None, indices of the molecules that broke) after a device error."""
+    from . import inputs as I
+    cfg = I.ragged_batch(lengths, seed=seed)
+    p = D.dsdna_default_params(kT=float(kT), dt=sweep_dt(kT), seed=seed + 1000)
+    ctx = D.Context(p, cfg.n_bp, X=cfg.X, u=cfg.u, tether=np.ones(len(lengths), np.int32))
+    try:
+        for m, (f, g) in enumerate(loads):
+            ctx.set_external_force_torque(m, [0.0, 0.0, f], [0.0, 0.0, g])
+        acc = np.zeros((len(lengths), NO)); ns = 0
+        done = 0
+        try:
+            while done < steps:
+                ctx.step(every)
+                done += every
+                if done >= measure_from:
+                    for m in range(len(lengths)):
+                        o = ctx.observables(m, D.OBS_EXT | D.OBS_DENAT | D.OBS_TW)
+                        N = lengths[m]
+                        acc[m, 0] += o["rz"] / (0.34 * max(N - 1, 1))
+                        acc[m, 1] += (o["tw"] - o["tw_ideal"]) / o["tw_ideal"] if o["tw_ideal"] else 0.0
+                        acc[m, 2] += o["denat"]
+                    ns += 1
+        except D.DsdnaError as e:
+            if e.status not in ("EFENE", "ENAN"):
+                raise
+            bad = _broken_molecules(ctx, lengths, p.R0)
+            if not bad:
+                raise
+            return None, bad
+        return acc / max(ns, 1), None
+    finally:
+        ctx.close()
+
+
 def simulate_sweep(points, steps: int = 4000, measure_from: int = 2000, every: int = 200, seed: int = 0,
                    max_nt_per_context: int = 3_000_000):
     """Full simulations of the sweep points with the batched engine.
@@ -197,11 +259,12 @@ def simulate_sweep(points, steps: int = 4000, measure_from: int = 2000, every: i
     Every point is one tethered molecule of its length (relaxed helix along
     z, base pair 0 anchored) with force f e_z and torque Gamma e_z on its
     last base pair; points of one kT level run together in one context
-    (chunked by size).  The labels are the averages over the samples taken
-    every ``every`` steps from ``measure_from`` on of: R_z / (0.34 (N-1)),
-    (Tw - Tw0) / Tw0 and the denatured fraction.
+    (chunked by size) at the timestep ``sweep_dt(kT)``.  The labels are the
+    averages over the samples taken every ``every`` steps from
+    ``measure_from`` on of: R_z / (0.34 (N-1)), (Tw - Tw0) / Tw0 and the
+    denatured fraction.  A molecule whose backbone breaks (FENE reaches R0)
+    gets NaN labels and its group is run again without it.
     """
-    from . import inputs as I
     pts = np.asarray(points, np.float64)
     out = np.zeros((len(pts), NO))
     order = np.argsort(pts[:, 3], kind="stable")
@@ -217,25 +280,94 @@ def simulate_sweep(points, steps: int = 4000, measure_from: int = 2000, every: i
         if cur:
             groups.append((kT, cur))
     for gi, (kT, idx) in enumerate(groups):
-        lengths = [int(pts[i, 2]) for i in idx]
-        cfg = I.ragged_batch(lengths, seed=seed + gi)
-        p = D.dsdna_default_params(kT=float(kT), seed=seed + 1000 + gi)
-        ctx = D.Context(p, cfg.n_bp, X=cfg.X, u=cfg.u, tether=np.ones(len(idx), np.int32))
-        for m, i in enumerate(idx):
-            ctx.set_external_force_torque(m, [0.0, 0.0, pts[i, 0]], [0.0, 0.0, pts[i, 1]])
-        acc = np.zeros((len(idx), NO)); ns = 0
-        done = 0
-        while done < steps:
-            ctx.step(every)
-            done += every
-            if done >= measure_from:
-                for m in range(len(idx)):
-                    o = ctx.observables(m, D.OBS_EXT | D.OBS_DENAT | D.OBS_TW)
-                    N = lengths[m]
-                    acc[m, 0] += o["rz"] / (0.34 * max(N - 1, 1))
-                    acc[m, 1] += (o["tw"] - o["tw_ideal"]) / o["tw_ideal"] if o["tw_ideal"] else 0.0
-                    acc[m, 2] += o["denat"]
-                ns += 1
-        ctx.close()
-        out[idx] = acc / max(ns, 1)
+        idx = list(idx)
+        for _attempt in range(8):
+            if not idx:
+                break
+            lengths = [int(pts[i, 2]) for i in idx]
+            loads = [(pts[i, 0], pts[i, 1]) for i in idx]
+            lab, bad = _run_group(lengths, loads, kT, seed + gi, steps, measure_from, every)
+            if bad is None:
+                out[idx] = lab
+                break
+            for m in bad:
+                out[idx[m]] = np.nan
+            idx = [i for m, i in enumerate(idx) if m not in set(bad)]
+        else:
+            out[idx] = np.nan
     return out
+
+
+def _metrics(Y, T):
+    ok = np.isfinite(T).all(1)
+    Y, T = Y[ok], T[ok]
+    err = Y - T
+    rmse = np.sqrt((err ** 2).mean(0))
+    var = ((T - T.mean(0)) ** 2).mean(0)
+    r2 = 1.0 - (err ** 2).mean(0) / np.maximum(var, 1e-30)
+    return {"rmse": rmse.tolist(), "r2": r2.tolist()}
+
+
+def run_sweep_study(n_train: int = 2000, n_test: int = 200, n_query: int = 100, length=(500, 20000),
+                    steps: int = 4000, measure_from: int = 1000, every: int = 200, models: int = 4,
+                    iters: int = 3000, seed: int = 0) -> dict:
+    """Train on n_train simulated sweep points, evaluate on n_test held-out
+    simulated points; then add n_query points chosen by the committee or at
+    random and compare the held-out error of the two retrained surrogates."""
+    import time
+    import torch
+
+    def sim(pts, s):
+        t = time.perf_counter()
+        y = simulate_sweep(pts, steps=steps, measure_from=measure_from, every=every, seed=s)
+        torch.cuda.synchronize()
+        return y, time.perf_counter() - t
+
+    train = sample_points(n_train, seed, length)
+    test = sample_points(n_test, seed + 1, length)
+    Ttrain, t_train = sim(train, seed)
+    Ttest, t_test = sim(test, seed + 1)
+    sur = Surrogate(models, max_batch=max(4096, n_train + n_query), seed=seed)
+    t = time.perf_counter()
+    sur.fit(train, Ttrain, iters=iters)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t
+    t = time.perf_counter()
+    Y, sd = sur.predict(test)
+    t_pred = time.perf_counter() - t
+    base = _metrics(Y, Ttest)
+    # query by committee vs random additions of the same size
+    cand = sample_points(20 * n_query, seed + 2, length)
+    pick = sur.select(cand, n_query)
+    rnd = np.random.default_rng(seed + 3).choice(len(cand), n_query, replace=False)
+    Tq, _ = sim(cand[pick], seed + 4)
+    Tr, _ = sim(cand[rnd], seed + 5)
+    sur.fit(np.concatenate([train, cand[pick]]), np.concatenate([Ttrain, Tq]), iters=iters)
+    qbc = _metrics(sur.predict(test)[0], Ttest)
+    sur.fit(np.concatenate([train, cand[rnd]]), np.concatenate([Ttrain, Tr]), iters=iters)
+    random_add = _metrics(sur.predict(test)[0], Ttest)
+    sur.close()
+    return {
+        "train_points": n_train, "test_points": n_test, "lengths_bp": list(length), "steps": steps,
+        "outputs": ["extension/contour", "excess twist (Tw-Tw0)/Tw0", "denatured fraction"],
+        "label_spread": Ttest.std(0).tolist(),
+        "held_out": base, "after_committee_queries": qbc, "after_random_queries": random_add,
+        "seconds": {"simulate_train": t_train, "simulate_test": t_test, "fit": t_fit, "predict_test": t_pred},
+        "simulation_s_per_point": t_test / n_test, "surrogate_s_per_point": t_pred / n_test,
+        "speedup_per_point": (t_test / n_test) / max(t_pred / n_test, 1e-12),
+    }
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="sweep surrogate study (train / held-out / committee queries)")
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=200)
+    ap.add_argument("--query", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--min-bp", type=int, default=500)
+    ap.add_argument("--max-bp", type=int, default=20000)
+    ap.add_argument("--iters", type=int, default=3000)
+    a = ap.parse_args()
+    print(json.dumps(run_sweep_study(a.train, a.test, a.query, (a.min_bp, a.max_bp), a.steps, iters=a.iters)))

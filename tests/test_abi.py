@@ -44,6 +44,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         "dsdna_allocator": [f for f, _ in dsdna.dsdna_allocator._fields_],
         "dsdna_obs": [f for f, _ in dsdna.dsdna_obs._fields_],
         "dsdna_info": [f for f, _ in dsdna.dsdna_info._fields_],
+        "dsdna_prof": [f for f, _ in dsdna.dsdna_prof._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for s, fs in fields.items():

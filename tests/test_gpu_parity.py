@@ -212,6 +212,26 @@ def test_checkpoint_resume_is_bitwise(prec):
         h.close()
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_profiled_steps_follow_the_same_trajectory(prec):
+    """dsdna_step_profiled queues the same kernels launch by launch: the
+    state equals the graph-driven run bit for bit, and every launch is timed."""
+    cfg = I.c1_linear(300)
+    a = ctx_for(cfg, prec, seed=5)
+    b = ctx_for(cfg, prec, seed=5)
+    a.step(120)
+    n0 = b.info()["engine_launches"]
+    pr = b.step_profiled(120)
+    assert pr["steps"] == 120 and b.step_counter == 120
+    assert pr["engine_launches"] >= 1 and pr["engine_ms"] > 0.0
+    assert pr["rebuild_launches"] >= 1 and pr["rebuild_ms"] > 0.0
+    assert b.info()["engine_launches"] - n0 == pr["engine_launches"]
+    assert a.info()["engine_launches"] >= pr["engine_launches"]
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    a.close(); b.close()
+
+
 def test_broken_backbone_reports_efene_and_poisons():
     cfg = I.c1_linear(40)
     X = cfg.X.copy()
@@ -223,6 +243,8 @@ def test_broken_backbone_reports_efene_and_poisons():
     with pytest.raises(D.DsdnaError) as e2:
         ctx.step(1)
     assert e2.value.status == "ESTATE"
+    Xpm = ctx.get_state()[0]          # post-mortem read shows the broken bond
+    assert np.abs(Xpm - X).max() < 1e-6
     ctx.set_state(-1, X=cfg.X, u=cfg.u)
     Fb, Fp = ctx.compute_forces()
     assert np.isfinite(Fb).all()
