@@ -108,6 +108,16 @@ class ClockSampler:
         except Exception:
             self.p = None
 
+    def wait_first(self, timeout: float = 10.0):
+        """Block until nvidia-smi has written its first sample: its start-up
+        holds the driver long enough to starve a short timed region."""
+        t0 = time.time()
+        while self.p is not None and time.time() - t0 < timeout:
+            self.f.flush()
+            if os.path.getsize(self.f.name) > 0:
+                return
+            time.sleep(0.05)
+
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -294,6 +304,8 @@ def main():
         torch.cuda.synchronize()
 
     sampler = ClockSampler(gpu_uuid(torch, local)) if rank == 0 else None
+    if sampler:
+        sampler.wait_first()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)

@@ -200,19 +200,24 @@ def sweep_dt(kT: float) -> float:
 
 
 def _broken_molecules(ctx, lengths, R0):
-    """Molecules whose post-mortem state holds a backbone bond at or beyond
-    0.98 R0 or a non-finite coordinate."""
+    """Molecules to drop after a device error: those with a non-finite
+    coordinate or a backbone bond beyond 0.9 R0 in the post-mortem state, else
+    the one whose longest bond is closest to R0 (the state is the one after
+    the update of the step whose forces saw the bond at R0)."""
     X, V, u, Om = ctx.get_state()
     off = np.concatenate([[0], np.cumsum(lengths)]) * 2
-    bad = []
+    bad, score = [], np.zeros(len(lengths))
     for m in range(len(lengths)):
         Xm, um = X[off[m]:off[m + 1]], u[off[m]:off[m + 1]]
-        if not (np.isfinite(Xm).all() and np.isfinite(V[off[m]:off[m + 1]]).all()):
+        if not (np.isfinite(Xm).all() and np.isfinite(V[off[m]:off[m + 1]]).all() and np.isfinite(um).all()):
             bad.append(m)
             continue
         b = Xm - 0.25 * um
-        if len(b) > 2 and np.linalg.norm(b[2:] - b[:-2], axis=1).max() >= 0.98 * R0:
+        score[m] = np.linalg.norm(b[2:] - b[:-2], axis=1).max() / R0 if len(b) > 2 else 0.0
+        if score[m] >= 0.9:
             bad.append(m)
+    if not bad:
+        bad = [int(np.argmax(score))]
     return bad
 
 
@@ -243,10 +248,7 @@ def _run_group(lengths, loads, kT, seed, steps, measure_from, every):
         except D.DsdnaError as e:
             if e.status not in ("EFENE", "ENAN"):
                 raise
-            bad = _broken_molecules(ctx, lengths, p.R0)
-            if not bad:
-                raise
-            return None, bad
+            return None, _broken_molecules(ctx, lengths, p.R0)
         return acc / max(ns, 1), None
     finally:
         ctx.close()
