@@ -1,12 +1,13 @@
 // engine.cuh -- device side of the dsDNA engine (sm_103a).
 //
 // One persistent cooperative kernel advances the single-nucleotide dsDNA
-// model of Fosado et al. (arXiv:1608.03722): per step it evaluates every
-// interaction of App. A (Eqs. 9-15, Table 1) on chain segments staged in
-// shared memory, adds the typed WCA pairs of a full neighbour list, applies
-// the loads of Sec. 4, and integrates App. A Eq. 8 with the step of Eq. 16.
-// The cell/neighbour rebuild runs inside the same kernel between bounded grid
-// barriers when a bead moved more than skin/2.
+// model of Fosado et al. (arXiv:1608.03722): per step every warp walks its
+// strip of the chain, evaluates every interaction of App. A (Eqs. 9-15,
+// Table 1) on tiles staged in shared memory, adds the typed WCA pairs of a
+// full neighbour list, applies the loads of Sec. 4, and integrates App. A
+// Eq. 8 with the step of Eq. 16; a bounded grid barrier separates the steps.
+// It stops when a bead moved more than skin/2; five ordinary kernels then
+// rebuild the cell and neighbour lists before the next launch.
 //
 // Precision (Real = float, "mixed"): the FP64 centre positions X and
 // velocities V are the integrator's accumulators; forces, orientation u and

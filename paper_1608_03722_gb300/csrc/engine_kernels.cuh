@@ -7,24 +7,27 @@
 namespace dsdna {
 
 // ---------------------------------------------------------------- shared memory
+// Each warp walks a contiguous strip of slots in tiles of SEG = 32 and keeps
+// the positions it staged and the owner terms it computed in rings of RING
+// entries indexed by slot (mod RING), so a tile stages 32 new slots and
+// computes 32 new owners; the warp synchronises with __syncwarp only.
+constexpr int SEG = 32;
+constexpr int RING = 64;
+
 template <class Real>
 struct SegSmem {
-  SPos<Real>* pos;   // [W + 8]  slots base-4 .. base+W+3
-  int* flg;          // [W + 8]
-  Real* cs;          // [W + 4][6] forces of owner terms on the owner (bead xyz, patch xyz)
-  Real* cn;          // [W + 4][6] ... on the owner's next nucleotide
-  Real* cp;          // [W + 4][3] ... on the owner's previous patch (bending)
+  SPos<Real>* pos;   // [RING] staged slots
+  int* flg;          // [RING] topology words of the staged slots
+  Real* cs;          // [6][RING] forces of owner terms on the owner (bead xyz, patch xyz)
+  Real* cn;          // [6][RING] ... on the owner's next nucleotide
+  Real* cp;          // [3][RING] ... on the owner's previous patch (bending)
 };
-
-// Each warp owns a segment of SEG = 32 slots and a private slice of shared
-// memory, so the segment pass synchronises with __syncwarp only.
-constexpr int SEG = 32;
 
 template <class Real>
 __host__ __device__ inline size_t seg_warp_bytes() {
-  size_t b = sizeof(SPos<Real>) * (SEG + 8) + sizeof(int) * (SEG + 8);
+  size_t b = sizeof(SPos<Real>) * RING + sizeof(int) * RING;
   b = (b + 15) & ~(size_t)15;
-  b += sizeof(Real) * (size_t)(SEG + 4) * 15;
+  b += sizeof(Real) * (size_t)RING * 15;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -38,12 +41,12 @@ __device__ __forceinline__ SegSmem<Real> carve(unsigned char* raw, int /*T*/) {
   unsigned char* w = raw + seg_warp_bytes<Real>() * (threadIdx.x >> 5);
   SegSmem<Real> s;
   s.pos = reinterpret_cast<SPos<Real>*>(w);
-  s.flg = reinterpret_cast<int*>(w + sizeof(SPos<Real>) * (SEG + 8));
-  size_t off = sizeof(SPos<Real>) * (SEG + 8) + sizeof(int) * (SEG + 8);
+  s.flg = reinterpret_cast<int*>(w + sizeof(SPos<Real>) * RING);
+  size_t off = sizeof(SPos<Real>) * RING + sizeof(int) * RING;
   off = (off + 15) & ~(size_t)15;
   s.cs = reinterpret_cast<Real*>(w + off);
-  s.cn = s.cs + (size_t)(SEG + 4) * 6;
-  s.cp = s.cn + (size_t)(SEG + 4) * 6;
+  s.cn = s.cs + (size_t)RING * 6;
+  s.cp = s.cn + (size_t)RING * 6;
   return s;
 }
 
@@ -553,23 +556,26 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
   }
 }
 
-// ---------------------------------------------------------------- segment pass
+// ---------------------------------------------------------------- strip pass
+__device__ __forceinline__ int ring(int64_t g) { return (int)(g & (RING - 1)); }
+
+// Bonded terms owned by slot o (ring index ri): the step o -> next along its
+// strand (FENE + WCA, Morse, dihedral, planarity) and the bending angle at o.
+// Forces go to the owner (cs), its next nucleotide (cn) and the previous
+// patch (cp), so each term is evaluated once.
 template <class Real>
-__device__ __forceinline__ void owner_terms(const KArgs<Real>& a, const SegSmem<Real>& sm, int oi, unsigned& fl,
+__device__ __forceinline__ void owner_terms(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t o, unsigned& fl,
                                             Real* E, Real* W) {
-  const int pi = oi + 2;                // position index of the owner
-  const int f = sm.flg[pi];
-  Real* cs = sm.cs + 6 * oi;
-  Real* cn = sm.cn + 6 * oi;
-  Real* cp = sm.cp + 3 * oi;
+  const int ri = ring(o);
+  const int f = sm.flg[ri];
   V3<Real> sb{0, 0, 0}, sp{0, 0, 0}, nb{0, 0, 0}, np{0, 0, 0}, pp{0, 0, 0};
   if (f & F_NEXT) {
-    const int dir = (pi & 1) ? -2 : 2;  // strand A (even slot) runs up, strand B down
-    const SPos<Real>& o = sm.pos[pi];
-    const SPos<Real>& q = sm.pos[pi + dir];
+    const int dir = (o & 1) ? -2 : 2;   // strand A (even slot) runs up, strand B down
+    const SPos<Real> so = sm.pos[ri];
+    const SPos<Real> sq = sm.pos[ring(o + dir)];
     const Real h = a.c.h;
-    const V3<Real> uo = uvec(o), uq = uvec(q);
-    const V3<Real> Rq = rel(o, q);
+    const V3<Real> uo = uvec(so), uq = uvec(sq);
+    const V3<Real> Rq = rel(so, sq);
     const V3<Real> bo = -h * uo, po = h * uo, bq = Rq - h * uq, pq = Rq + h * uq;
     // FENE + WCA, Morse
     V3<Real> fb = t_fene(a.c, bq - bo, fl, E);
@@ -588,17 +594,55 @@ __device__ __forceinline__ void owner_terms(const KArgs<Real>& a, const SegSmem<
     sp += f1; nb += f2; np -= (f1 + f2);
     if (W) { vir_add(W, po, f1); vir_add(W, bq, f2); vir_add(W, pq, -(f1 + f2)); }
     if (f & F_PREV) {
-      const SPos<Real>& r = sm.pos[pi - dir];
-      const V3<Real> pr = rel(o, r) + h * uvec(r);
+      const SPos<Real> sr = sm.pos[ring(o - dir)];
+      const V3<Real> pr = rel(so, sr) + h * uvec(sr);
       V3<Real> g1, g2;
       t_bend(a.c, pr - po, pq - po, g1, g2, E);
       pp += g1; np += g2; sp -= (g1 + g2);
       if (W) { vir_add(W, pr, g1); vir_add(W, pq, g2); vir_add(W, po, -(g1 + g2)); }
     }
   }
-  cs[0] = sb.x; cs[1] = sb.y; cs[2] = sb.z; cs[3] = sp.x; cs[4] = sp.y; cs[5] = sp.z;
-  cn[0] = nb.x; cn[1] = nb.y; cn[2] = nb.z; cn[3] = np.x; cn[4] = np.y; cn[5] = np.z;
-  cp[0] = pp.x; cp[1] = pp.y; cp[2] = pp.z;
+  sm.cs[0 * RING + ri] = sb.x; sm.cs[1 * RING + ri] = sb.y; sm.cs[2 * RING + ri] = sb.z;
+  sm.cs[3 * RING + ri] = sp.x; sm.cs[4 * RING + ri] = sp.y; sm.cs[5 * RING + ri] = sp.z;
+  sm.cn[0 * RING + ri] = nb.x; sm.cn[1 * RING + ri] = nb.y; sm.cn[2 * RING + ri] = nb.z;
+  sm.cn[3 * RING + ri] = np.x; sm.cn[4 * RING + ri] = np.y; sm.cn[5 * RING + ri] = np.z;
+  sm.cp[0 * RING + ri] = pp.x; sm.cp[1 * RING + ri] = pp.y; sm.cp[2 * RING + ri] = pp.z;
+}
+
+// MODE_ENERGY: per-term energies and virial of one owner or nucleotide, added
+// in FP64 to its molecule.
+template <class Real>
+__device__ __forceinline__ void flush_energy(const KArgs<Real>& a, int mol, Real* E, Real* W) {
+  double* dst = a.eout + EOUT_STRIDE * mol;
+  for (int k = 0; k < NTERMS; ++k) if (E[k] != (Real)0) atomicAdd(dst + k, (double)E[k]);
+  for (int k = 0; k < 6; ++k) if (W[k] != (Real)0) atomicAdd(dst + NTERMS + k, (double)W[k]);
+}
+
+// Stage slot g (ring entry) or an empty slot outside [0, n).
+template <class Real>
+__device__ __forceinline__ void stage_slot(const KArgs<Real>& a, const SegSmem<Real>& sm, int cur, int64_t g) {
+  const int ri = ring(g);
+  if (g >= 0 && g < a.n) {
+    load_slot(a, cur, g, sm.pos[ri]);
+    sm.flg[ri] = a.topo[g];
+  } else {
+    sm.flg[ri] = 0;
+  }
+}
+
+// Owner o's terms; MODE_ENERGY adds them to its molecule when `count`.
+template <class Real, int MODE>
+__device__ __forceinline__ void owner_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t o, bool count,
+                                           unsigned& fl) {
+  if constexpr (MODE == MODE_ENERGY) {
+    Real E[NTERMS], W[6];
+    for (int k = 0; k < NTERMS; ++k) E[k] = 0;
+    for (int k = 0; k < 6; ++k) W[k] = 0;
+    owner_terms(a, sm, o, fl, count ? E : nullptr, count ? W : nullptr);
+    if (count) flush_energy(a, sm.flg[ring(o)] >> 8, E, W);
+  } else {
+    owner_terms<Real>(a, sm, o, fl, nullptr, nullptr);
+  }
 }
 
 template <class Real>
@@ -615,61 +659,40 @@ __device__ __forceinline__ void store_state(const KArgs<Real>& a, int nxt, int64
   }
 }
 
+// Forces on nucleotide g from the owner rings, its H-bond and its list
+// pairs, then (MODE_STEP) its Langevin update; MODE_FORCES writes the site
+// forces, MODE_ENERGY adds its per-nucleotide energies.
 template <class Real, int MODE>
-__device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t base, int cur, int64_t step,
-                             unsigned& fl, double* eacc) {
-  const int T = SEG, tid = threadIdx.x & 31;
+__device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t g, int cur,
+                                                int64_t step, unsigned& fl) {
   const int nxt = cur ^ 1;
-  // 1. stage slots base-4 .. base+T+3
-  for (int s = tid; s < T + 8; s += T) {
-    const int64_t g = base - 4 + s;
-    if (g >= 0 && g < a.n) {
-      load_slot(a, cur, g, sm.pos[s]);
-      sm.flg[s] = a.topo[g];
-    } else {
-      sm.flg[s] = 0;
-    }
-  }
-  __syncwarp();
-  // 2. bonded terms of owners base-2 .. base+T+1
   Real Eb[NTERMS];
   Real Wb[6];
   if constexpr (MODE == MODE_ENERGY) {
     for (int k = 0; k < NTERMS; ++k) Eb[k] = 0;
     for (int k = 0; k < 6; ++k) Wb[k] = 0;
   }
-  for (int oi = tid; oi < T + 4; oi += T) {
-    const bool own = (oi >= 2 && oi < T + 2);   // energy of a term goes to its owner only once
-    if constexpr (MODE == MODE_ENERGY) {
-      owner_terms(a, sm, oi, fl, own ? Eb : nullptr, own ? Wb : nullptr);
-    } else {
-      owner_terms<Real>(a, sm, oi, fl, nullptr, nullptr);
-    }
-  }
-  __syncwarp();
-  // 3. own nucleotide
-  const int64_t g = base + tid;
-  if (g < a.n) {
-    const int pi = tid + 4, oi = tid + 2;
-    const int f = sm.flg[pi];
-    const SPos<Real>& me = sm.pos[pi];
+  {
+    const int ri = ring(g);
+    const int f = sm.flg[ri];
+    const SPos<Real>& me = sm.pos[ri];
     const Real h = a.c.h;
     const V3<Real> um = uvec(me);
-    V3<Real> Fb{sm.cs[6 * oi + 0], sm.cs[6 * oi + 1], sm.cs[6 * oi + 2]};
-    V3<Real> Fp{sm.cs[6 * oi + 3], sm.cs[6 * oi + 4], sm.cs[6 * oi + 5]};
-    const int dir = (pi & 1) ? -2 : 2;
+    V3<Real> Fb{sm.cs[0 * RING + ri], sm.cs[1 * RING + ri], sm.cs[2 * RING + ri]};
+    V3<Real> Fp{sm.cs[3 * RING + ri], sm.cs[4 * RING + ri], sm.cs[5 * RING + ri]};
+    const int dir = (g & 1) ? -2 : 2;
     if (f & F_PREV) {
-      const int op = oi - dir;
-      Fb += V3<Real>{sm.cn[6 * op + 0], sm.cn[6 * op + 1], sm.cn[6 * op + 2]};
-      Fp += V3<Real>{sm.cn[6 * op + 3], sm.cn[6 * op + 4], sm.cn[6 * op + 5]};
+      const int op = ring(g - dir);
+      Fb += V3<Real>{sm.cn[0 * RING + op], sm.cn[1 * RING + op], sm.cn[2 * RING + op]};
+      Fp += V3<Real>{sm.cn[3 * RING + op], sm.cn[4 * RING + op], sm.cn[5 * RING + op]};
     }
     if (f & F_NEXT) {
-      const int on = oi + dir;
-      Fp += V3<Real>{sm.cp[3 * on + 0], sm.cp[3 * on + 1], sm.cp[3 * on + 2]};
+      const int on = ring(g + dir);
+      Fp += V3<Real>{sm.cp[0 * RING + on], sm.cp[1 * RING + on], sm.cp[2 * RING + on]};
     }
     // hydrogen bond with the partner (App. A Eq. 10), broken beyond rc
     {
-      const SPos<Real>& q = sm.pos[pi ^ 1];
+      const SPos<Real>& q = sm.pos[ring(g ^ 1)];
       const V3<Real> d = rel(me, q) + h * uvec(q) - h * um;   // patch_q - patch_me
       const Real r2 = dot(d, d);
       if (r2 <= a.c.rchb2) {
@@ -677,7 +700,7 @@ __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int6
         if (a.c.r0hb != (Real)0) k2 *= (Real)1 - a.c.r0hb * rsqrt_(r2);
         Fp += k2 * d;
         if constexpr (MODE == MODE_ENERGY) {
-          if ((pi & 1) == 0) {
+          if ((g & 1) == 0) {
             const Real r = sqrt_(r2);
             const Real rc = sqrt_(a.c.rchb2);
             Eb[2] += a.c.khb * ((r - a.c.r0hb) * (r - a.c.r0hb) - (rc - a.c.r0hb) * (rc - a.c.r0hb));
@@ -742,7 +765,7 @@ __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int6
       const Real tn2 = dot(Tq, Tq);
       if (tn2 > (Real)0) {
         const V3<Real> th = rsqrt_(tn2) * Tq;
-        V3<Real> rho = (Real)-0.5 * rel(me, sm.pos[pi ^ 1]);   // centre offset from the pair centre
+        V3<Real> rho = (Real)-0.5 * rel(me, sm.pos[ring(g ^ 1)]);   // centre offset from the pair centre
         rho -= dot(rho, th) * th;
         const Real S = (Real)2 * dot(rho, rho);
         if (S > (Real)1e-12) Fe += ((Real)1 / S) * cross(Tq, rho);
@@ -837,16 +860,33 @@ __device__ void segment_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int6
       }
     }
   }
-  if constexpr (MODE == MODE_ENERGY) {
-    // per-thread FP64 accumulation by molecule of the owner
-    if (g < a.n) {
-      const int mol = sm.flg[tid + 4] >> 8;
-      double* dst = a.eout + EOUT_STRIDE * mol;
-      for (int k = 0; k < NTERMS; ++k) if (Eb[k] != (Real)0) atomicAdd(dst + k, (double)Eb[k]);
-      for (int k = 0; k < 6; ++k) if (Wb[k] != (Real)0) atomicAdd(dst + NTERMS + k, (double)Wb[k]);
-    }
+  if constexpr (MODE == MODE_ENERGY) flush_energy(a, sm.flg[ring(g)] >> 8, Eb, Wb);
+}
+
+// One warp's strip: tiles [t0, t1) of SEG slots.  The prologue stages slots
+// s0-4 .. s0+3 and computes owners s0-2 .. s0+1; every tile at base B then
+// stages slots B+4 .. B+35, computes owners B+2 .. B+33 (one per lane) and
+// finishes nucleotides B .. B+31, whose terms come from owners B-2 .. B+33.
+// An owner's energy is counted by the strip that holds its slot.
+template <class Real, int MODE>
+__device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t t0, int64_t t1, int cur,
+                           int64_t step, unsigned& fl) {
+  if (t0 >= t1) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t s0 = t0 * SEG;
+  const int64_t s1 = t1 * SEG < a.n ? t1 * SEG : a.n;
+  if (lane < 8) stage_slot(a, sm, cur, s0 - 4 + lane);
+  __syncwarp();
+  if (lane < 4) owner_pass<Real, MODE>(a, sm, s0 - 2 + lane, lane >= 2 && s0 - 2 + lane < s1, fl);
+  for (int64_t t = t0; t < t1; ++t) {
+    const int64_t B = t * SEG;
+    __syncwarp();
+    stage_slot(a, sm, cur, B + 4 + lane);
+    __syncwarp();
+    owner_pass<Real, MODE>(a, sm, B + 2 + lane, B + 2 + lane < s1, fl);
+    __syncwarp();
+    if (B + lane < s1) nucleotide_pass<Real, MODE>(a, sm, B + lane, cur, step, fl);
   }
-  (void)eacc;
   __syncwarp();
 }
 
@@ -907,8 +947,8 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 1) engine_kernel(
     __syncthreads();
     unsigned fl = 0;
     const int64_t wpb = blockDim.x >> 5;
-    for (int64_t seg = blockIdx.x * wpb + (threadIdx.x >> 5); seg < a.nseg; seg += gridDim.x * wpb)
-      segment_pass<Real, MODE>(a, sm, seg * (int64_t)SEG, cur, step, fl, nullptr);
+    const int64_t nw = gridDim.x * wpb, w = blockIdx.x * wpb + (threadIdx.x >> 5);
+    strip_pass<Real, MODE>(a, sm, w * a.nseg / nw, (w + 1) * a.nseg / nw, cur, step, fl);
     if (fl) atomicOr(&s_fl, fl);
     __syncthreads();
     if (MODE != MODE_STEP) {
