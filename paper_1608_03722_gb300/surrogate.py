@@ -352,7 +352,9 @@ def run_sweep_study(n_train: int = 2000, n_test: int = 200, n_query: int = 100, 
     return {
         "train_points": n_train, "test_points": n_test, "lengths_bp": list(length), "steps": steps,
         "outputs": ["extension/contour", "excess twist (Tw-Tw0)/Tw0", "denatured fraction"],
-        "label_spread": Ttest.std(0).tolist(),
+        "label_spread": np.nanstd(Ttest, 0).tolist(),
+        "dropped_points": {"train": int((~np.isfinite(Ttrain).all(1)).sum()),
+                           "test": int((~np.isfinite(Ttest).all(1)).sum())},
         "held_out": base, "after_committee_queries": qbc, "after_random_queries": random_add,
         "seconds": {"simulate_train": t_train, "simulate_test": t_test, "fit": t_fit, "predict_test": t_pred},
         "simulation_s_per_point": t_test / n_test, "surrogate_s_per_point": t_pred / n_test,
