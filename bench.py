@@ -344,12 +344,16 @@ def main():
     # neighbours per bead (full list), for the algorithmic byte count
     nbar = 2.0 * len(ctx.neighbor_pairs()) / cfg.n_nt
 
-    # algorithmic bytes per nucleotide-step of the fused force + Langevin kernel (DESIGN.md):
-    # state X,V (FP64) + u, Omega (FP32) read and written, position mirror read and written,
-    # topology word, neighbour count and list entries
-    state = 48 + 24 if prec == D.PREC_MIXED else 96
-    mirror = 32 if prec == D.PREC_MIXED else 48
-    b_nt = 2 * state + 2 * mirror + 4 + 4 + 4 * nbar
+    # algorithmic bytes per nucleotide-step of the fused force + Langevin kernel:
+    # mixed: read X, V (FP64 24 + 24), Omega (FP32 12), kref 12, mirror + orientation
+    # (16 + 16), topology 4, count 4, image 4 (periodic), list 4 n; write X, V, Omega,
+    # next mirror + orientation (24 + 24 + 12 + 16 + 16).  FP64: X, u, V, Omega 24 each
+    # read and written, kref 12, topology, count, image 4 each.
+    periodic = 1 if cfg.box[0] > 0 else 0
+    if prec == D.PREC_MIXED:
+        b_nt = (112 + 4 * periodic) + 92 + 4 * nbar
+    else:
+        b_nt = (96 + 12 + 8 + 4 * periodic) + 96 + 4 * nbar
     steps_per_launch = prof["steps"] / max(prof["engine_launches"], 1)
     per_launch_bytes = b_nt * cfg.n_nt * steps_per_launch
     launch_s = prof["engine_ms"] * 1e-3 / max(prof["engine_launches"], 1)

@@ -111,7 +111,7 @@ typedef struct dsdna_params {
   double skin;                           /* neighbour-list skin, at most 1 nm (0: default 0.3) */
   int precision;                         /* DSDNA_PREC_MIXED (FP32 forces, FP64 X/V) or DSDNA_PREC_FP64 */
   int max_neighbors;                     /* neighbour capacity per bead (0: default 32; at most 32) */
-  int block_threads;                     /* nucleotides per CTA segment (0: default 256; 64..256, multiple of 32) */
+  int block_threads;                     /* threads per CTA of the step kernel (0: default 256; 64..256, multiple of 32) */
   int blocks_per_sm;                     /* persistent CTAs per SM (0: as many as fit) */
   int steps_per_graph;                   /* steps per captured CUDA graph launch (0: default 50) */
 } dsdna_params;

@@ -18,6 +18,10 @@ LIB = os.path.join(PKG, "libdsdna.so")
 SOURCES = ["capi.cu", "kern_mixed.cu", "kern_fp64.cu", "observables.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
+# The FP32 force kernels use the hardware reciprocal, square root and exponential
+# (1-2 ulp): far inside the 1e-5 relative force tolerance, and a third fewer
+# instructions in the bonded terms than the correctly rounded sequences.
+EXTRA = {"kern_mixed.cu": ["-use_fast_math"]}
 
 
 def nvcc() -> str:
@@ -48,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def one(src: str) -> tuple[str, str]:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *EXTRA.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

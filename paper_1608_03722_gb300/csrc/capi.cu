@@ -26,7 +26,7 @@ template <class Real> cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_
 
 using namespace dsdna;
 
-static constexpr int64_t SEG_SLOTS = 32;   // slots per warp segment of the engine kernel
+static constexpr int64_t SEG_SLOTS = 32;   // slots per tile of the engine kernel (a warp walks a strip of tiles)
 
 static thread_local std::string g_create_error;
 
@@ -326,7 +326,7 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
     if (s->n_bp[m] < 1) return fail(nullptr, DSDNA_EINVAL, "molecule with fewer than one base pair");
     tot += s->n_bp[m];
   }
-  if (2 * tot >= ((int64_t)1 << 27)) return fail(nullptr, DSDNA_EINVAL, "more than 2^27 nucleotides");
+  if (2 * tot >= ((int64_t)1 << ENT_J_BITS)) return fail(nullptr, DSDNA_EINVAL, "more than 2^26 nucleotides");
   const bool per = p->box[0] > 0.0;
   for (int k = 0; k < 3; ++k)
     if ((p->box[k] > 0.0) != per) return fail(nullptr, DSDNA_EINVAL, "box must be periodic in all or no directions");
@@ -918,7 +918,7 @@ extern "C" int dsdna_neighbor_pairs(dsdna_ctx* c, int64_t cap, int64_t* pi, int6
   int64_t k = 0;
   for (size_t i = 0; i < nn; ++i)
     for (int q = 0; q < nc[i]; ++q) {
-      const int64_t j = nb[(size_t)q * nn + i] & ((1 << NBR_J_BITS) - 1);
+      const int64_t j = nb[(size_t)q * nn + i] & ENT_JMASK;
       if ((int64_t)i < j) {
         if (k < cap) { pi[k] = (int64_t)i; pj[k] = j; }
         ++k;

@@ -32,7 +32,18 @@ constexpr int NTERMS = 10;
 constexpr int EOUT_STRIDE = 16;           // energy terms + 6 virial
 constexpr float FIX_SCALE_F = 1.0f / 536870912.0f;  // 2^-29
 constexpr double FIX_SCALE_D = 1.0 / 536870912.0;
-constexpr int NBR_J_BITS = 27;
+constexpr int NBR_J_BITS = 27;   // slot field of a cell-sorted bead word (bit 27: steric flag)
+
+// Neighbour-list entry: partner slot j in the low ENT_J_BITS bits, then the
+// minimum-image shift s + 1 in {0, 1, 2} of each axis in a 2-bit field
+// (x at bit 26, y at 28, z at 30).  No entry has all bits set (a field never
+// holds 3), so -1 marks "no entry".
+constexpr int ENT_J_BITS = 26;
+constexpr int ENT_JMASK = (1 << ENT_J_BITS) - 1;
+__host__ __device__ __forceinline__ int ent_make(int j, int sx, int sy, int sz) {
+  return (int)((unsigned)j | ((unsigned)(sx + 1) << 26) | ((unsigned)(sy + 1) << 28) | ((unsigned)(sz + 1) << 30));
+}
+__host__ __device__ __forceinline__ int ent_shift(int e, int c) { return (int)(((unsigned)e >> (26 + 2 * c)) & 3u) - 1; }
 
 struct GridBar {
   unsigned count;

@@ -1,5 +1,5 @@
 // engine_kernels.cuh -- persistent kernel of the dsDNA engine: neighbour-list
-// rebuild phases and the fused force + Langevin segment pass.  Included by
+// rebuild phases and the fused force + Langevin strip pass.  Included by
 // kern_mixed.cu (Real = float) and kern_fp64.cu (Real = double).
 #pragma once
 #include "engine.cuh"
@@ -339,12 +339,11 @@ __device__ void list_one_bead(const KArgs<Real>& a, int64_t t, unsigned& fl) {
           else continue;
           if (r2 >= rl2) continue;
           if (a.n_mol > 1 && __float_as_int(a.wpos[j].w) != mol) continue;
-          const int code = (sc[0] + 1) + 3 * (sc[1] + 1) + 9 * (sc[2] + 1);
-          const int ent = j | (code << NBR_J_BITS);
+          const int ent = ent_make(j, sc[0], sc[1], sc[2]);
           ++total;
           if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed
             int qq = cnt++;
-            while (qq > 0 && (list[qq - 1] & JMASK) > j) { list[qq] = list[qq - 1]; --qq; }
+            while (qq > 0 && (list[qq - 1] & ENT_JMASK) > j) { list[qq] = list[qq - 1]; --qq; }
             list[qq] = ent;
           }
         }
@@ -379,11 +378,11 @@ __device__ __forceinline__ void consider(const KArgs<Real>& a, const float* p, i
   else return;
   if (r2 >= rl2) return;
   if (a.n_mol > 1 && __float_as_int(a.wpos[j].w) != mol) return;
-  const int ent = j | (((sc[0] + 1) + 3 * (sc[1] + 1) + 9 * (sc[2] + 1)) << NBR_J_BITS);
+  const int ent = ent_make(j, sc[0], sc[1], sc[2]);
   ++total;
   if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed
     int q = cnt++;
-    while (q > 0 && (list[q - 1] & JMASK) > j) { list[q] = list[q - 1]; --q; }
+    while (q > 0 && (list[q - 1] & ENT_JMASK) > j) { list[q] = list[q - 1]; --q; }
     list[q] = ent;
   }
 }
@@ -400,8 +399,7 @@ constexpr int LIST_WARPS = 8;
 constexpr int LIST_CB = 16;
 constexpr int LIST_CAP = 32;
 
-// typed pair test; returns the list entry, or -1 (no entry has all bits set:
-// image codes stop at 26) -- entries with codes >= 16 are negative ints
+// typed pair test; returns the list entry (ent_make), or -1
 template <class Real>
 __device__ __forceinline__ int pair_entry(const KArgs<Real>& a, float4 me, float4 o, int mol) {
   const int JMASK = (1 << NBR_J_BITS) - 1;
@@ -413,19 +411,17 @@ __device__ __forceinline__ int pair_entry(const KArgs<Real>& a, float4 me, float
   else if (((gw & jw) >> NBR_J_BITS) & 1) rl2 = a.c.rl_ss2;
   else return -1;
   float d[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
-  int code = 13;
+  int sc[3] = {0, 0, 0};
   if (a.periodic) {
-    code = 0;
-    const int mul[3] = {1, 3, 9};
     for (int c = 0; c < 3; ++c) {
       const float s = -rintf(d[c] * a.invLf[c]);
       d[c] = fmaf(s, a.Lf[c], d[c]);
-      code += ((int)s + 1) * mul[c];
+      sc[c] = (int)s;
     }
   }
   if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] >= rl2) return -1;
   if (a.n_mol > 1 && __float_as_int(a.wpos[j].w) != mol) return -1;
-  return j | (code << NBR_J_BITS);
+  return ent_make(j, sc[0], sc[1], sc[2]);
 }
 
 template <class Real, int CAPMAX>
@@ -544,7 +540,7 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
           for (int x = 1; x < cnt; ++x) {     // order by partner slot: the force sum order is fixed
             const int v = e[x];
             int y = x;
-            while (y > 0 && (e[y - 1] & JMASK) > (v & JMASK)) { e[y] = e[y - 1]; --y; }
+            while (y > 0 && (e[y - 1] & ENT_JMASK) > (v & ENT_JMASK)) { e[y] = e[y - 1]; --y; }
             e[y] = v;
           }
           for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.n + g] = e[q];
@@ -715,8 +711,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       const int img_me = a.periodic ? a.img[g] : 0;
       for (int q = 0; q < nn; ++q) {
         const int ent = a.nbr[(size_t)q * a.n + g];
-        const int j = ent & ((1 << NBR_J_BITS) - 1);
-        const int code = (unsigned)ent >> NBR_J_BITS;
+        const int j = ent & ENT_JMASK;
         V3<Real> R;
         V3<Real> uj;
         if constexpr (sizeof(Real) == 4) {
@@ -726,9 +721,9 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
           unsigned dx = (unsigned)kj.x - (unsigned)me.kx, dy = (unsigned)kj.y - (unsigned)me.ky,
                    dz = (unsigned)kj.z - (unsigned)me.kz;
           if (a.periodic) {
-            const int mx = img_comp(img_me, 0) - img_comp(kj.w, 0) + (code % 3) - 1;
-            const int my = img_comp(img_me, 1) - img_comp(kj.w, 1) + (code / 3) % 3 - 1;
-            const int mz = img_comp(img_me, 2) - img_comp(kj.w, 2) + code / 9 - 1;
+            const int mx = img_comp(img_me, 0) - img_comp(kj.w, 0) + ent_shift(ent, 0);
+            const int my = img_comp(img_me, 1) - img_comp(kj.w, 1) + ent_shift(ent, 1);
+            const int mz = img_comp(img_me, 2) - img_comp(kj.w, 2) + ent_shift(ent, 2);
             dx += (unsigned)mx * a.Lfix[0]; dy += (unsigned)my * a.Lfix[1]; dz += (unsigned)mz * a.Lfix[2];
           }
           R = V3<float>{(float)(int)dx * FIX_SCALE_F, (float)(int)dy * FIX_SCALE_F, (float)(int)dz * FIX_SCALE_F};
@@ -739,9 +734,9 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
           R = V3<double>{X[j] - me.x, X[a.n + j] - me.y, X[2 * a.n + j] - me.z};
           if (a.periodic) {
             const int ij = a.img[j];
-            R.x += (double)(img_comp(img_me, 0) - img_comp(ij, 0) + (code % 3) - 1) * a.L[0];
-            R.y += (double)(img_comp(img_me, 1) - img_comp(ij, 1) + (code / 3) % 3 - 1) * a.L[1];
-            R.z += (double)(img_comp(img_me, 2) - img_comp(ij, 2) + code / 9 - 1) * a.L[2];
+            R.x += (double)(img_comp(img_me, 0) - img_comp(ij, 0) + ent_shift(ent, 0)) * a.L[0];
+            R.y += (double)(img_comp(img_me, 1) - img_comp(ij, 1) + ent_shift(ent, 1)) * a.L[1];
+            R.z += (double)(img_comp(img_me, 2) - img_comp(ij, 2) + ent_shift(ent, 2)) * a.L[2];
           }
         }
         const V3<Real> d = R - h * uj + h * um;   // bead_j - bead_me
