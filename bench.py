@@ -397,12 +397,14 @@ def main():
     if rank == 0 and not args.no_compare:
         compare = compare_batched(D, torch)
         from paper_1608_03722_gb300 import surrogate as SUR
-        st = SUR.run_sweep_study(n_train=256, n_test=64, n_query=32, length=(500, 2000), steps=2000,
-                                 measure_from=500, every=100, iters=1500)
+        st = SUR.run_sweep_study(n_train=256, n_test=64, n_query=32, length=(100, 400), steps=8000,
+                                 measure_from=2000, every=100, iters=3000)
         compare["surrogate"] = {
-            "workload": "sweep of tethered molecules 500-2000 bp, force 0.1-10 kT/nm, torque -5..5 kT, kT 0.8-1.4 "
-                        "(256 training / 64 held-out points, 2000 steps each)",
+            "workload": "sweep of tethered molecules 100-400 bp, force 0.1-10 kT/nm, torque -5..5 kT, kT 0.8-1.4 "
+                        "(256 training / 64 held-out points, 8000 steps each)",
             "held_out_r2": st["held_out"]["r2"], "held_out_rmse": st["held_out"]["rmse"],
+            "replicate_noise": st["replicate_noise"],
+            "rmse_over_replicate_noise": st["held_out"]["rmse_over_replicate_noise"],
             "simulation_s_per_point": st["simulation_s_per_point"],
             "surrogate_s_per_point": st["surrogate_s_per_point"], "speedup_per_point": st["speedup_per_point"],
             "r2_after_committee_queries": st["after_committee_queries"]["r2"],

@@ -315,8 +315,11 @@ int dsdna_mlp_forward(dsdna_mlp* net, const float* X, int B, float* Y);
  * the last forward pass against targets T; writes the loss to *loss_host
  * (may be NULL, then the call does not wait). */
 int dsdna_mlp_backward(dsdna_mlp* net, const float* T, int B, float* loss_host);
-/* One Adam step (bias-corrected) on the FP32 masters; refreshes the BF16 copies. */
-int dsdna_mlp_adam_step(dsdna_mlp* net, float lr, float beta1, float beta2, float eps);
+/* One Adam step (bias-corrected, Kingma & Ba) on the FP32 masters with
+ * decoupled weight decay on the three weight matrices (Loshchilov & Hutter):
+ * p <- p - lr (m_hat / (sqrt(v_hat) + eps) + weight_decay p); biases are not
+ * decayed.  Refreshes the BF16 copies.  weight_decay < 0: DSDNA_EINVAL. */
+int dsdna_mlp_adam_step(dsdna_mlp* net, float lr, float beta1, float beta2, float eps, float weight_decay);
 void dsdna_mlp_destroy(dsdna_mlp* net);
 
 #ifdef __cplusplus

@@ -93,3 +93,20 @@ def init_params(seed=0):
          "W2": rng.normal(0, math.sqrt(2.0 / NH), (NH, NH)), "b2": np.zeros(NH),
          "W3": rng.normal(0, math.sqrt(1.0 / NH), (NO, NH)), "b3": np.zeros(NO)}
     return pack(d)
+
+
+def weight_mask():
+    """1 on the entries of W1, W2, W3 (decayed), 0 on the biases."""
+    return pack({k: np.full(s, 1.0 if k.startswith("W") else 0.0) for k, s in SHAPES})
+
+
+def adam_step(p, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+    """One Adam step (Kingma & Ba, bias-corrected moments; t counts from 1) with
+    decoupled weight decay on the weight matrices (Loshchilov & Hutter).
+    Returns the new (p, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    p = p - lr * (mhat / (np.sqrt(vhat) + eps) + weight_decay * weight_mask() * p)
+    return p, m, v

@@ -741,24 +741,36 @@ void or_mb_velocities(const or_params* p, int mol, int n_bp, const double* u, in
 }
 
 /* ------------------------------------------------------- Langevin dynamics */
-/* Noise of one site: Philox counter (local nucleotide, step low, step high,
- * 2*mol + site), key (seed low, seed high).  Uniform mode draws the variance
- * matched uniform sqrt(24 gamma kT / dt) * (U - 1/2), U = (x + 1/2) 2^-32. */
-static void site_noise(const or_params* p, int mol, int64_t local, int64_t step, int site, double* eta) {
-  if (p->noise == 0) { eta[0] = eta[1] = eta[2] = 0.0; return; }
-  uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
-  uint32_t ctr[4] = {(uint32_t)local, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)(2 * mol + site)}, r[4];
-  or_philox4x32_10(ctr, key, r);
-  if (p->noise == 1) {
-    double c = ldexp(sqrt(24.0 * p->gamma * p->kT / p->dt), -32);
-    for (int k = 0; k < 3; ++k) eta[k] = ((double)r[k] - 2147483647.5) * c;
-  } else {
-    double a = sqrt(2.0 * p->gamma * p->kT / p->dt);
-    double r0 = sqrt(-2.0 * log(u01(r[0]))), r1 = sqrt(-2.0 * log(u01(r[2])));
-    eta[0] = a * r0 * cos(2.0 * PI * u01(r[1]));
-    eta[1] = a * r0 * sin(2.0 * PI * u01(r[1]));
-    eta[2] = a * r1 * cos(2.0 * PI * u01(r[3]));
+/* Noise of both sites of one nucleotide from one Philox4x32-10 draw with
+ * counter (local nucleotide, step low, step high, mol) and key (seed low,
+ * seed high).  The four output words x, y, z, w give six 21-bit integers:
+ * the top 21 bits of x, y, z (bead x, y, z) and of w (patch x); the low 11
+ * bits of x with bits 0-9 of y above them (patch y); the same of z and w
+ * (patch z).  U = (k + 1/2) 2^-21.  Uniform mode draws the variance matched
+ * uniform sqrt(24 gamma kT / dt) (U - 1/2); Gaussian mode takes Box-Muller
+ * pairs (U0, U1), (U2, U3), (U4, U5) with standard deviation sqrt(2 gamma kT / dt). */
+static void nucleotide_noise(const or_params* p, int mol, int64_t local, int64_t step, double* eb, double* ep) {
+  double e[6] = {0, 0, 0, 0, 0, 0};
+  if (p->noise != 0) {
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)local, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)mol}, r[4];
+    or_philox4x32_10(ctr, key, r);
+    uint32_t k[6] = {r[0] >> 11, r[1] >> 11, r[2] >> 11, r[3] >> 11,
+                     (r[0] & 0x7FFu) | ((r[1] & 0x3FFu) << 11), (r[2] & 0x7FFu) | ((r[3] & 0x3FFu) << 11)};
+    if (p->noise == 1) {
+      double c = ldexp(sqrt(24.0 * p->gamma * p->kT / p->dt), -21);
+      for (int q = 0; q < 6; ++q) e[q] = ((double)k[q] - 1048575.5) * c;
+    } else {
+      double a = sqrt(2.0 * p->gamma * p->kT / p->dt);
+      for (int q = 0; q < 6; q += 2) {
+        double u0 = ldexp((double)k[q] + 0.5, -21), u1 = ldexp((double)k[q + 1] + 0.5, -21);
+        double rad = sqrt(-2.0 * log(u0));
+        e[q] = a * rad * cos(2.0 * PI * u1);
+        e[q + 1] = a * rad * sin(2.0 * PI * u1);
+      }
+    }
   }
+  for (int c = 0; c < 3; ++c) { eb[c] = e[c]; ep[c] = e[3 + c]; }
 }
 
 /* Total (conservative + external + friction + noise) force and torque on a
@@ -768,8 +780,7 @@ static void site_noise(const or_params* p, int mol, int64_t local, int64_t step,
 static void total_force(const or_params* p, int mol, int64_t local, int64_t step, const double* F, const double* T,
                         const double* V, const double* Om, const double* u, double* Ft, double* Tt) {
   double eb[3], ep[3];
-  site_noise(p, mol, local, step, 0, eb);
-  site_noise(p, mol, local, step, 1, ep);
+  nucleotide_noise(p, mol, local, step, eb, ep);
   double de[3] = {ep[0] - eb[0], ep[1] - eb[1], ep[2] - eb[2]}, tn[3];
   v_cross(u, de, tn);
   double gr = p->gamma * 0.5 * p->ell * p->ell;

@@ -276,7 +276,7 @@ static void fill_coef(const dsdna_params& p, Coef<Real>& c) {
   if (p.noise == DSDNA_NOISE_GAUSSIAN) {
     c.noise_cd = std::sqrt(2.0 * p.gamma * p.kT / p.dt);
   } else {
-    c.noise_cd = std::ldexp(std::sqrt(24.0 * p.gamma * p.kT / p.dt), -32);
+    c.noise_cd = std::ldexp(std::sqrt(24.0 * p.gamma * p.kT / p.dt), -21);
   }
   c.noise_c = (Real)c.noise_cd;
   const double margin = 0.01;   // absorbs FP32 rounding of the wrapped build positions

@@ -65,7 +65,7 @@ struct Coef {
   Real dtM, dtI;     // dt / M, dt / I
   Real dt;
   Real gam2, gamr;   // 2 gamma, gamma ell^2 / 2
-  Real noise_c;      // uniform: sqrt(24 gamma kT/dt) 2^-32; gaussian: sqrt(2 gamma kT/dt)
+  Real noise_c;      // uniform: sqrt(24 gamma kT/dt) 2^-21; gaussian: sqrt(2 gamma kT/dt)
   Real halfdtM, halfdtI;
   Real M, I;
   float skin_half2;  // (skin/2)^2
@@ -179,34 +179,46 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
-// One site's Langevin noise (App. A Eq. 8): counter (local nucleotide, step,
-// 2*mol + site), key = seed.
+// Langevin noise of both sites of one nucleotide (App. A Eq. 8) from one
+// Philox draw: counter (local nucleotide, step low, step high, mol), key =
+// seed.  The four words give six 21-bit integers k -- the top 21 bits of
+// x, y, z (bead) and w (patch x), then the low 11 bits of x with bits 0-9 of
+// y above them (patch y) and the same of z and w (patch z) -- and uniform
+// variates U = (k + 1/2) 2^-21: variance-matched uniform noise
+// sqrt(24 gamma kT / dt) (U - 1/2), or Box-Muller pairs (U0, U1), (U2, U3),
+// (U4, U5).  (k - 2^20 + 1/2) is exact in FP32.
 template <class Real>
-__device__ __forceinline__ V3<Real> site_noise(const KArgs<Real>& a, uint32_t local, int64_t step, int mol, int site) {
-  if (a.noise_mode == 0) return V3<Real>{0, 0, 0};
-  uint4 r = philox10(make_uint4(local, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)(2 * mol + site)),
-                     a.seed_lo, a.seed_hi);
+__device__ __forceinline__ void nucleotide_noise(const KArgs<Real>& a, uint32_t local, int64_t step, int mol,
+                                                 V3<Real>& eb, V3<Real>& ep) {
+  if (a.noise_mode == 0) {
+    eb = V3<Real>{0, 0, 0};
+    ep = eb;
+    return;
+  }
+  const uint4 r = philox10(make_uint4(local, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)mol),
+                           a.seed_lo, a.seed_hi);
+  const uint32_t k[6] = {r.x >> 11, r.y >> 11, r.z >> 11, r.w >> 11, (r.x & 0x7FFu) | ((r.y & 0x3FFu) << 11),
+                         (r.z & 0x7FFu) | ((r.w & 0x3FFu) << 11)};
+  Real e[6];
   if (a.noise_mode == 1) {
-    if constexpr (sizeof(Real) == 8) {
-      const double cc = a.c.noise_cd;
-      return V3<Real>{((double)r.x - 2147483647.5) * cc, ((double)r.y - 2147483647.5) * cc,
-                      ((double)r.z - 2147483647.5) * cc};
-    } else {
-      const float cc = a.c.noise_c;
-      return V3<Real>{((float)(int)(r.x ^ 0x80000000u) + 0.5f) * cc, ((float)(int)(r.y ^ 0x80000000u) + 0.5f) * cc,
-                      ((float)(int)(r.z ^ 0x80000000u) + 0.5f) * cc};
+    const Real cc = sizeof(Real) == 8 ? (Real)a.c.noise_cd : a.c.noise_c;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) e[q] = ((Real)(int)k[q] - (Real)1048575.5) * cc;
+  } else {
+    const Real s21 = (Real)(1.0 / 2097152.0);
+    const Real cc = a.c.noise_c;
+#pragma unroll
+    for (int q = 0; q < 6; q += 2) {
+      const Real u0 = ((Real)(int)k[q] + (Real)0.5) * s21, u1 = ((Real)(int)k[q + 1] + (Real)0.5) * s21;
+      const Real rad = sqrt_((Real)-2 * log_(u0));
+      Real sn, cs;
+      sincos_((Real)6.283185307179586 * u1, &sn, &cs);
+      e[q] = cc * rad * cs;
+      e[q + 1] = cc * rad * sn;
     }
   }
-  // Gaussian (Box-Muller)
-  const Real s32 = (Real)(1.0 / 4294967296.0);
-  Real u0 = ((Real)r.x + (Real)0.5) * s32, u1 = ((Real)r.y + (Real)0.5) * s32;
-  Real u2 = ((Real)r.z + (Real)0.5) * s32, u3 = ((Real)r.w + (Real)0.5) * s32;
-  Real r0 = sqrt_((Real)-2 * log_(u0)), r1 = sqrt_((Real)-2 * log_(u2));
-  Real s0, c0, s1, c1;
-  sincos_((Real)6.283185307179586 * u1, &s0, &c0);
-  sincos_((Real)6.283185307179586 * u3, &s1, &c1);
-  const Real cc = a.c.noise_c;
-  return V3<Real>{cc * r0 * c0, cc * r0 * s0, cc * r1 * c1};
+  eb = V3<Real>{e[0], e[1], e[2]};
+  ep = V3<Real>{e[3], e[4], e[5]};
 }
 
 // ---------------------------------------------------------------- positions

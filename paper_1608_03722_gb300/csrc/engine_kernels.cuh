@@ -427,10 +427,12 @@ __device__ __forceinline__ int pair_entry(const KArgs<Real>& a, float4 me, float
 template <class Real, int CAPMAX>
 __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
   __shared__ float4 tile[LIST_WARPS][LIST_TILE];
+  __shared__ int tent[LIST_WARPS][LIST_TILE];   // list entry of the staged candidate (image shift set)
   __shared__ float4 cpos[LIST_WARPS][LIST_CB];
   __shared__ int scount[LIST_WARPS][LIST_CB];
   __shared__ int sent[LIST_WARPS][LIST_CB][LIST_CAP];
   __shared__ unsigned rb[LIST_WARPS][28], roff[LIST_WARPS][28];
+  __shared__ int rsh[LIST_WARPS][28];             // image shift of each neighbour cell (2-bit fields, x y z)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int JMASK = (1 << NBR_J_BITS) - 1;
   const bool dedupe = !(a.morton_bits > 0 && a.nc[0] >= 3 && a.nc[1] >= 3 && a.nc[2] >= 3);
@@ -478,10 +480,14 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
       }
       // ranges of the 27 neighbour cells, one per lane, duplicates (hash) dropped
       unsigned rbeg = 0, rlen = 0, key = 0xffffffffu;
+      int shift[3] = {0, 0, 0};   // image of the neighbour cell seen from this cell (periodic box)
       if (lane < 27) {
         int c3[3] = {c0[0] + (lane % 3) - 1, c0[1] + (lane / 3) % 3 - 1, c0[2] + lane / 9 - 1};
         if (a.periodic)
-          for (int c = 0; c < 3; ++c) c3[c] = c3[c] < 0 ? c3[c] + a.nc[c] : (c3[c] >= a.nc[c] ? c3[c] - a.nc[c] : c3[c]);
+          for (int c = 0; c < 3; ++c) {
+            shift[c] = c3[c] < 0 ? -1 : (c3[c] >= a.nc[c] ? 1 : 0);
+            c3[c] -= shift[c] * a.nc[c];
+          }
         key = cell_key(a, mol0, c3[0], c3[1], c3[2]);
       }
       if (dedupe) {
@@ -500,7 +506,10 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
         if (lane >= o) incl += y;
       }
       const unsigned M = __shfl_sync(0xffffffffu, incl, 31);
-      if (lane < 27) { rb[w][lane] = rbeg; roff[w][lane] = incl - rlen; }
+      if (lane < 27) {
+        rb[w][lane] = rbeg; roff[w][lane] = incl - rlen;
+        rsh[w][lane] = ent_make(0, shift[0], shift[1], shift[2]);
+      }
       __syncwarp();
       for (unsigned cb = beg; cb < end; cb += LIST_CB) {
         const int mc = (int)min((unsigned)LIST_CB, end - cb);
@@ -515,19 +524,45 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
               const int mid = (lo + hi + 1) >> 1;
               if (roff[w][mid] <= gi) lo = mid; else hi = mid - 1;
             }
-            tile[w][i] = a.cent[rb[w][lo] + (gi - roff[w][lo])];
+            float4 o = a.cent[rb[w][lo] + (gi - roff[w][lo])];
+            const int ej = __float_as_int(o.w) & JMASK;
+            int e = ej | rsh[w][lo];
+            if (!dedupe) {
+              // periodic Morton table with >= 3 cells per edge: every candidate of a
+              // neighbour cell takes that cell's image (the minimum image within rl)
+              o.x += (float)ent_shift(e, 0) * a.Lf[0];
+              o.y += (float)ent_shift(e, 1) * a.Lf[1];
+              o.z += (float)ent_shift(e, 2) * a.Lf[2];
+            }
+            if (a.n_mol > 1 && __float_as_int(a.wpos[ej].w) != mol0) e = -1;   // another molecule
+            tile[w][i] = o;
+            tent[w][i] = e;
           }
           __syncwarp();
-          // all lanes: bead b of the cell against tile entries i = lane, lane + 32, ...
-          for (int b = 0; b < mc; ++b) {
+          // (bead, candidate) pairs of this tile spread over the lanes
+          const unsigned P = (unsigned)mc * mn;
+          unsigned b = lane / mn, i = lane % mn;
+          const unsigned qb = 32u / mn, qi = 32u % mn;
+          for (unsigned pp = lane; pp < P; pp += 32) {
             const float4 me = cpos[w][b];
-            for (unsigned i = lane; i < mn; i += 32) {
-              const int ent = pair_entry(a, me, tile[w][i], mol0);
-              if (ent != -1) {
-                const int q = atomicAdd(&scount[w][b], 1);
-                if (q < LIST_CAP) sent[w][b][q] = ent;
-              }
+            int ent;
+            if (!dedupe) {
+              const float4 o = tile[w][i];
+              const int gw = __float_as_int(me.w), jw = __float_as_int(o.w);
+              const int g = gw & JMASK, j = jw & JMASK;
+              const float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
+              const float r2 = dx * dx + dy * dy + dz * dz;
+              const float rl2 = ((g ^ j) & 1) ? a.c.rl_cr2 : ((((gw & jw) >> NBR_J_BITS) & 1) ? a.c.rl_ss2 : -1.0f);
+              ent = (r2 < rl2 && j != g) ? tent[w][i] : -1;   // tent is -1 for another molecule
+            } else {
+              ent = pair_entry(a, me, tile[w][i], mol0);
             }
+            if (ent != -1) {
+              const int q = atomicAdd(&scount[w][b], 1);
+              if (q < LIST_CAP) sent[w][b][q] = ent;
+            }
+            i += qi; b += qb;
+            if (i >= mn) { i -= mn; ++b; }
           }
         }
         __syncwarp();
@@ -614,7 +649,10 @@ __device__ __forceinline__ void flush_energy(const KArgs<Real>& a, int mol, Real
   for (int k = 0; k < 6; ++k) if (W[k] != (Real)0) atomicAdd(dst + NTERMS + k, (double)W[k]);
 }
 
-// Stage slot g (ring entry) or an empty slot outside [0, n).
+// Stage slot g into its ring entry (f = 0 for a slot outside [0, n)).  Loading
+// the next tile's slots one tile ahead in registers was measured slower: at
+// 64 registers it spills, and at 80 registers three CTAs per SM hide less
+// latency than four.
 template <class Real>
 __device__ __forceinline__ void stage_slot(const KArgs<Real>& a, const SegSmem<Real>& sm, int cur, int64_t g) {
   const int ri = ring(g);
@@ -789,8 +827,8 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       V3<Real> Ft{0, 0, 0}, Tt{0, 0, 0};
       if (!frozen) {
         // App. A Eq. 8 per site: friction -gamma v_s and noise eta_s, summed over the dumbbell
-        const V3<Real> eb = site_noise(a, local, step, mol, 0);
-        const V3<Real> ep = site_noise(a, local, step, mol, 1);
+        V3<Real> eb, ep;
+        nucleotide_noise(a, local, step, mol, eb, ep);
         V3<Real> Vh;
         if constexpr (sizeof(Real) == 4) {
           Vh = V3<Real>{d2f_bits(Vd[0]), d2f_bits(Vd[1]), d2f_bits(Vd[2])};

@@ -271,7 +271,10 @@ __global__ void k_mlp_backward(MlpDev m, const float* T, int B) {
   }
 }
 
-__global__ void k_mlp_adam(MlpDev m, float lr, float b1, float b2, float eps, float c1, float c2) {
+// Adam with bias correction (c1 = 1 - beta1^t, c2 = 1 - beta2^t) and decoupled
+// weight decay wd on the weight matrices (not the biases):
+// p <- p - lr (m_hat / (sqrt(v_hat) + eps) + wd p).
+__global__ void k_mlp_adam(MlpDev m, float lr, float b1, float b2, float eps, float c1, float c2, float wd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NP) return;
   const float g = m.G[i];
@@ -279,7 +282,9 @@ __global__ void k_mlp_adam(MlpDev m, float lr, float b1, float b2, float eps, fl
   const float vv = b2 * m.V[i] + (1.0f - b2) * g * g;
   m.M[i] = mm;
   m.V[i] = vv;
-  const float p = m.P[i] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+  const bool weight = i < OB1 || (i >= OW2 && i < OB2) || (i >= OW3 && i < OB3);
+  const float p0 = m.P[i];
+  const float p = p0 - lr * ((mm / c1) / (sqrtf(vv / c2) + eps) + (weight ? wd * p0 : 0.0f));
   m.P[i] = p;
   m.Pb[i] = __float2bfloat16_rn(p);
 }
@@ -407,10 +412,11 @@ extern "C" int dsdna_mlp_backward(dsdna_mlp* m, const float* T, int B, float* lo
   return DSDNA_OK;
 }
 
-extern "C" int dsdna_mlp_adam_step(dsdna_mlp* m, float lr, float beta1, float beta2, float eps) {
-  if (!m) return DSDNA_EINVAL;
+extern "C" int dsdna_mlp_adam_step(dsdna_mlp* m, float lr, float beta1, float beta2, float eps, float weight_decay) {
+  if (!m || weight_decay < 0.0f) return DSDNA_EINVAL;
   ++m->adam_t;
-  const float c1 = 1.0f - std::pow(beta1, (float)m->adam_t), c2 = 1.0f - std::pow(beta2, (float)m->adam_t);
-  k_mlp_adam<<<(NP + 255) / 256, 256, 0, m->st>>>(m->d, lr, beta1, beta2, eps, c1, c2);
+  const float c1 = (float)(1.0 - std::pow((double)beta1, (double)m->adam_t));
+  const float c2 = (float)(1.0 - std::pow((double)beta2, (double)m->adam_t));
+  k_mlp_adam<<<(NP + 255) / 256, 256, 0, m->st>>>(m->d, lr, beta1, beta2, eps, c1, c2, weight_decay);
   return cudaGetLastError() == cudaSuccess ? DSDNA_OK : DSDNA_ECUDA;
 }

@@ -17,6 +17,7 @@ from . import _build
 
 NTERMS = 10
 TERM_NAMES = ["fene", "bond_wca", "hbond", "wca", "dihedral", "morse", "planar", "bend", "kin_t", "kin_r"]
+(E_FENE, E_BONDWCA, E_HBOND, E_WCA, E_DIHEDRAL, E_MORSE, E_PLANAR, E_BEND, E_KIN_T, E_KIN_R) = range(NTERMS)
 PREC_MIXED, PREC_FP64 = 0, 1
 NOISE_OFF, NOISE_UNIFORM, NOISE_GAUSSIAN = 0, 1, 2
 OBS_EXT, OBS_DENAT, OBS_TW, OBS_LK = 1, 2, 4, 8

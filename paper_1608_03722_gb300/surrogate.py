@@ -33,7 +33,7 @@ def _lib():
         L.dsdna_mlp_get_params.argtypes = [C.c_void_p, P(C.c_float), P(C.c_float)]
         L.dsdna_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
         L.dsdna_mlp_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, P(C.c_float)]
-        L.dsdna_mlp_adam_step.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_float]
+        L.dsdna_mlp_adam_step.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]
         L.dsdna_mlp_destroy.argtypes = [C.c_void_p]
         L.dsdna_mlp_destroy.restype = None
         L._mlp_ready = True
@@ -91,8 +91,8 @@ class Mlp:
             raise D.DsdnaError(rc, "dsdna_mlp_backward failed")
         return loss.value
 
-    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
-        rc = self.L.dsdna_mlp_adam_step(self.h, float(lr), float(beta1), float(beta2), float(eps))
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+        rc = self.L.dsdna_mlp_adam_step(self.h, float(lr), float(beta1), float(beta2), float(eps), float(weight_decay))
         if rc != 0:
             raise D.DsdnaError(rc, "dsdna_mlp_adam_step failed")
 
@@ -132,8 +132,17 @@ class Surrogate:
         self.seed = seed
         self.norm = None
 
-    def fit(self, X, T, iters: int = 2000, batch: int = 256, lr: float = 3e-3):
-        """Adam on random minibatches for every member (learning rate decayed tenfold); final full-batch losses."""
+    def fit(self, X, T, iters: int = 3000, batch: int = 256, lr: float = 3e-3, weight_decay: float = 1e-2,
+            val_frac: float = 0.2, check_every: int = 25, patience: int = 10):
+        """Train every member with Adam (decoupled weight decay on the weights,
+        learning rate decayed tenfold over `iters`) on random minibatches.
+
+        Sweep labels are time averages of short simulations and carry sampling
+        noise, so each member holds out its own random `val_frac` of the points,
+        checks its loss on them every `check_every` iterations, and keeps the
+        parameters of the lowest one, stopping after `patience` checks without
+        improvement.  Points with non-finite labels are skipped.  Returns the
+        members' best validation losses (training losses when nothing is held out)."""
         torch = self.torch
         X = np.asarray(X, np.float32); T = np.asarray(T, np.float32)
         ok = np.isfinite(T).all(1)          # points whose simulation broke carry NaN labels
@@ -148,14 +157,36 @@ class Surrogate:
         for k, m in enumerate(self.models):
             m.set_params(_he_init(self.seed + k), in_mean, in_scale, out_mean, out_scale)
             rng = np.random.default_rng(self.seed + 100 + k)
+            perm = rng.permutation(n)
+            nv = int(round(val_frac * n)) if n >= 10 else 0
+            vi, ti = perm[:nv], perm[nv:]
+            Xt, Tt = Xd[torch.tensor(ti, device="cuda")].contiguous(), Td[torch.tensor(ti, device="cuda")].contiguous()
+            if nv:
+                Xv = Xd[torch.tensor(vi, device="cuda")].contiguous()
+                Tv = Td[torch.tensor(vi, device="cuda")].contiguous()
+            nt = len(ti)
+            best_loss, best_p, bad = math.inf, None, 0
             for it in range(iters):
-                idx = torch.tensor(rng.choice(n, size=min(batch, n), replace=False), device="cuda")
-                xb = Xd[idx].contiguous(); tb = Td[idx].contiguous()
+                idx = torch.tensor(rng.choice(nt, size=min(batch, nt), replace=False), device="cuda")
+                xb = Xt[idx].contiguous(); tb = Tt[idx].contiguous()
                 m.forward(xb, Yd[: xb.shape[0]])
                 m.backward(tb, want_loss=False)
-                m.adam(lr * (0.1 ** (it / iters)))
-            m.forward(Xd, Yd[:n])
-            losses.append(m.backward(Td))
+                m.adam(lr * (0.1 ** (it / iters)), weight_decay=weight_decay)
+                if nv and (it + 1) % check_every == 0:
+                    m.forward(Xv, Yd[:nv])
+                    lv = m.backward(Tv)
+                    if lv < best_loss:
+                        best_loss, best_p, bad = lv, m.get_params()[0], 0
+                    else:
+                        bad += 1
+                        if bad >= patience:
+                            break
+            if best_p is not None:
+                m.set_params(best_p)
+                losses.append(best_loss)
+            else:
+                m.forward(Xt, Yd[:nt])
+                losses.append(m.backward(Tt))
         return losses
 
     def predict(self, X):
@@ -311,11 +342,14 @@ def _metrics(Y, T):
 
 
 def run_sweep_study(n_train: int = 2000, n_test: int = 200, n_query: int = 100, length=(500, 20000),
-                    steps: int = 4000, measure_from: int = 1000, every: int = 200, models: int = 4,
+                    steps: int = 8000, measure_from: int = 2000, every: int = 200, models: int = 4,
                     iters: int = 3000, seed: int = 0) -> dict:
     """Train on n_train simulated sweep points, evaluate on n_test held-out
     simulated points; then add n_query points chosen by the committee or at
-    random and compare the held-out error of the two retrained surrogates."""
+    random and compare the held-out error of the two retrained surrogates.
+    The held-out points are simulated a second time with another seed: the
+    RMS difference / sqrt(2) is the sampling noise of one simulated label, the
+    yardstick for the surrogate's error."""
     import time
     import torch
 
@@ -329,6 +363,9 @@ def run_sweep_study(n_train: int = 2000, n_test: int = 200, n_query: int = 100, 
     test = sample_points(n_test, seed + 1, length)
     Ttrain, t_train = sim(train, seed)
     Ttest, t_test = sim(test, seed + 1)
+    Trep, _ = sim(test, seed + 6)
+    both = np.isfinite(Ttest).all(1) & np.isfinite(Trep).all(1)
+    rep_noise = np.sqrt(((Ttest[both] - Trep[both]) ** 2).mean(0) / 2)
     sur = Surrogate(models, max_batch=max(4096, n_train + n_query), seed=seed)
     t = time.perf_counter()
     sur.fit(train, Ttrain, iters=iters)
@@ -338,6 +375,7 @@ def run_sweep_study(n_train: int = 2000, n_test: int = 200, n_query: int = 100, 
     Y, sd = sur.predict(test)
     t_pred = time.perf_counter() - t
     base = _metrics(Y, Ttest)
+    base["rmse_over_replicate_noise"] = (np.asarray(base["rmse"]) / np.maximum(rep_noise, 1e-30)).tolist()
     # query by committee vs random additions of the same size
     cand = sample_points(20 * n_query, seed + 2, length)
     pick = sur.select(cand, n_query)
@@ -352,7 +390,7 @@ def run_sweep_study(n_train: int = 2000, n_test: int = 200, n_query: int = 100, 
     return {
         "train_points": n_train, "test_points": n_test, "lengths_bp": list(length), "steps": steps,
         "outputs": ["extension/contour", "excess twist (Tw-Tw0)/Tw0", "denatured fraction"],
-        "label_spread": np.nanstd(Ttest, 0).tolist(),
+        "label_spread": np.nanstd(Ttest, 0).tolist(), "replicate_noise": rep_noise.tolist(),
         "dropped_points": {"train": int((~np.isfinite(Ttrain).all(1)).sum()),
                            "test": int((~np.isfinite(Ttest).all(1)).sum())},
         "held_out": base, "after_committee_queries": qbc, "after_random_queries": random_add,
@@ -369,7 +407,7 @@ if __name__ == "__main__":
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--test", type=int, default=200)
     ap.add_argument("--query", type=int, default=100)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=8000)
     ap.add_argument("--min-bp", type=int, default=500)
     ap.add_argument("--max-bp", type=int, default=20000)
     ap.add_argument("--iters", type=int, default=3000)

@@ -78,6 +78,31 @@ def test_backward_matches_fp64_reference(torch):
     net.close()
 
 
+def test_adam_step_matches_fp64_reference(torch):
+    """Three Adam steps with decoupled weight decay: the kernel's FP32 masters
+    follow oracle/mlp.adam_step fed with the kernel's own gradients."""
+    rng = np.random.default_rng(9)
+    B = 200
+    p = (M.init_params(5) + rng.normal(0, 0.05, M.NP)).astype(np.float32)
+    X = np.stack([rng.uniform(0.1, 10, B), rng.uniform(-5, 5, B), rng.uniform(500, 2e4, B), rng.uniform(0.8, 1.4, B)], 1)
+    n = _norm()
+    T = n["out_mean"] + n["out_scale"] * rng.normal(0, 1, (B, 3))
+    net = _net(torch, p, n)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    Yd = torch.empty((B, 3), device="cuda")
+    pr, m, v = p.astype(np.float64), np.zeros(M.NP), np.zeros(M.NP)
+    for t in range(1, 4):
+        net.forward(Xd, Yd)
+        net.backward(Td, want_loss=False)
+        _, g = net.get_params()
+        net.adam(lr=1e-2, weight_decay=0.05)
+        pr, m, v = M.adam_step(pr, m, v, g.astype(np.float64), t, 1e-2, weight_decay=0.05)
+        pk, _ = net.get_params()
+        assert np.abs(pk - pr).max() < 1e-5 + 1e-5 * np.abs(pr).max(), (t, np.abs(pk - pr).max())
+    net.close()
+
+
 def test_training_reduces_the_loss_on_a_smooth_function(torch):
     rng = np.random.default_rng(3)
     N = 1500
@@ -93,26 +118,35 @@ def test_training_reduces_the_loss_on_a_smooth_function(torch):
 
 
 def test_surrogate_sweep_gains_over_full_simulation(torch):
-    """Surrogate on sweeps the engine itself simulates: on held-out points it
-    reproduces the simulated excess twist (linear in the applied torque) and
-    the extension trend, at a small fraction of the simulation cost; the
-    committee spread points at where to simulate next."""
-    train = S.sample_points(224, seed=1, length=(40, 160))
-    test = S.sample_points(32, seed=2, length=(40, 160))
-    Ttrain = S.simulate_sweep(train, steps=4000, measure_from=1000, every=100, seed=1)
+    """Surrogate on sweeps the engine itself simulates (tethered 100-400 bp
+    molecules, force, torque, length, kT; 8000 steps each).  A simulated label
+    is a time average with sampling noise, measured here by simulating the
+    held-out points twice with different seeds.  On held-out points the
+    committee's error stays within 1.6 times that replicate noise on every
+    output (R^2 above 0.4 / 0.6 / 0.35 for extension / twist / denatured
+    fraction) at under 5% of the simulation's cost, and the committee spread
+    picks distinct points to simulate next."""
+    kw = dict(steps=8000, measure_from=2000, every=100)
+    train = S.sample_points(224, seed=1, length=(100, 400))
+    test = S.sample_points(48, seed=2, length=(100, 400))
+    Ttrain = S.simulate_sweep(train, seed=1, **kw)
     t1 = time.perf_counter()
-    Ttest = S.simulate_sweep(test, steps=4000, measure_from=1000, every=100, seed=2)
+    Ta = S.simulate_sweep(test, seed=2, **kw)
     t_sim = time.perf_counter() - t1
-    assert np.isfinite(Ttrain).all() and np.isfinite(Ttest).all()
+    Tb = S.simulate_sweep(test, seed=3, **kw)
+    assert np.isfinite(Ttrain).all() and np.isfinite(Ta).all() and np.isfinite(Tb).all()
+    rep = np.sqrt(((Ta - Tb) ** 2).mean(0) / 2)       # sampling noise of one simulated label
     sur = S.Surrogate(n_models=4, max_batch=1024, seed=2)
-    sur.fit(train, Ttrain, iters=1200, batch=64, lr=3e-3)
+    sur.fit(train, Ttrain, iters=3000, batch=128)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     Y, sd = sur.predict(test)
     t_pred = time.perf_counter() - t2
-    r2 = 1 - ((Y - Ttest) ** 2).sum(0) / ((Ttest - Ttest.mean(0)) ** 2).sum(0)
-    assert r2[1] > 0.6, r2          # excess twist follows the torque (labels carry sampling noise)
+    err = np.sqrt(((Y - Ta) ** 2).mean(0))
+    r2 = 1 - ((Y - Ta) ** 2).sum(0) / ((Ta - Ta.mean(0)) ** 2).sum(0)
+    assert (err < 1.6 * rep).all(), (err, rep)
+    assert r2[0] > 0.4 and r2[1] > 0.6 and r2[2] > 0.35, r2
     assert t_pred < 0.05 * t_sim, (t_pred, t_sim)
-    pick = sur.select(S.sample_points(500, seed=3, length=(40, 160)), 20)
+    pick = sur.select(S.sample_points(500, seed=3, length=(100, 400)), 20)
     assert len(set(pick.tolist())) == 20
     sur.close()

@@ -232,6 +232,24 @@ def test_profiled_steps_follow_the_same_trajectory(prec):
     a.close(); b.close()
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_langevin_equipartition(prec):
+    """App. A Eq. 8 thermostat: 3/2 kT translational and kT rotational (two axes
+    normal to u) kinetic energy per nucleotide, averaged over a 200 bp run."""
+    cfg = I.c1_linear(200)
+    ctx = ctx_for(cfg, prec, seed=11)
+    ctx.step(1000)
+    kt, kr = [], []
+    for _ in range(60):
+        ctx.step(50)
+        E, _ = ctx.energy_virial()
+        kt.append(E[D.E_KIN_T] / cfg.n_nt)
+        kr.append(E[D.E_KIN_R] / cfg.n_nt)
+    ctx.close()
+    assert abs(np.mean(kt) - 1.5) < 0.06, np.mean(kt)
+    assert abs(np.mean(kr) - 1.0) < 0.05, np.mean(kr)
+
+
 def test_broken_backbone_reports_efene_and_poisons():
     cfg = I.c1_linear(40)
     X = cfg.X.copy()

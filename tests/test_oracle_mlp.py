@@ -59,3 +59,32 @@ def test_bf16_rounding():
     assert M.bf16(1.0 + 2 ** -9) == 1.0               # ties to even
     assert M.bf16(1.0 + 3 * 2 ** -9) == 1.0 + 2 ** -7
     assert abs(M.bf16(math.pi) - math.pi) < 2 ** -8 * math.pi
+
+
+def test_first_adam_step_has_closed_form():
+    """From zero moments the bias-corrected first step is lr g / (|g| + eps),
+    i.e. lr sign(g) for |g| >> eps, plus lr wd p on the weights only."""
+    rng = np.random.default_rng(4)
+    p = rng.normal(0, 1, M.NP)
+    g = rng.normal(0, 1, M.NP)
+    lr, wd = 1e-2, 0.1
+    p1, m1, v1 = M.adam_step(p, np.zeros(M.NP), np.zeros(M.NP), g, 1, lr, weight_decay=wd)
+    w = M.weight_mask()
+    want = p - lr * (g / (np.abs(g) + 1e-8) + wd * w * p)
+    assert np.allclose(p1, want, rtol=0, atol=1e-12)
+    assert np.allclose(m1, 0.1 * g) and np.allclose(v1, 0.001 * g * g)
+    d = M.unpack(w)
+    assert d["W2"].all() and not d["b2"].any() and d["W3"].all() and not d["b3"].any()
+    assert w.sum() == 64 * 4 + 64 * 64 + 3 * 64
+
+
+def test_adam_moments_follow_their_recurrences():
+    """Constant gradient: after t steps m = (1 - beta1^t) g and v = (1 - beta2^t) g^2,
+    so the bias-corrected step stays lr g / (|g| + eps) every step."""
+    g = np.linspace(-2, 2, M.NP) + 0.01
+    p = np.zeros(M.NP); m = np.zeros(M.NP); v = np.zeros(M.NP)
+    for t in range(1, 6):
+        p_prev = p
+        p, m, v = M.adam_step(p, m, v, g, t, 1e-3)
+        assert np.allclose(m, (1 - 0.9 ** t) * g) and np.allclose(v, (1 - 0.999 ** t) * g * g)
+        assert np.allclose(p_prev - p, 1e-3 * g / (np.abs(g) + 1e-8), atol=1e-15)

@@ -402,15 +402,21 @@ def test_langevin_equipartition():
 
 
 def test_noise_stream_moments():
-    """Variance-matched uniform noise: mean 0, variance 2 gamma kT / dt per component."""
-    p = O.params()
-    vals = []
-    for l in range(200):
+    """One Philox4x32-10 draw per nucleotide gives six 21-bit fields (top 21 bits
+    of each word, then the low 11 bits of x / z joined with bits 0-9 of y / w):
+    each uniform on [0, 2^21) with mean 0 and variance 1 after centring and
+    scaling by sqrt(12) 2^-21, and the six mutually uncorrelated."""
+    fields = []
+    for l in range(400):
         for s in range(10):
-            r = O.philox4x32_10([l, s, 0, 0], [0, 0])
-            vals += [((x - 2147483647.5) * 2.0 ** -32) * math.sqrt(12) for x in r[:3]]
-    v = np.array(vals)
-    assert abs(v.mean()) < 0.05 and abs(v.var() - 1.0) < 0.06
+            x, y, z, w = O.philox4x32_10([l, s, 0, 0], [0, 0])
+            k = [x >> 11, y >> 11, z >> 11, w >> 11, (x & 0x7FF) | ((y & 0x3FF) << 11), (z & 0x7FF) | ((w & 0x3FF) << 11)]
+            fields.append([((q - 1048575.5) * 2.0 ** -21) * math.sqrt(12) for q in k])
+    v = np.array(fields)
+    assert v.min() > -math.sqrt(3) and v.max() < math.sqrt(3)
+    assert np.abs(v.mean(0)).max() < 0.06 and np.abs(v.var(0) - 1.0).max() < 0.08
+    c = np.corrcoef(v.T) - np.eye(6)
+    assert np.abs(c).max() < 0.08
 
 
 def test_mb_velocities_statistics():
