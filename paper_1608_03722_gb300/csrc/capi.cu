@@ -61,6 +61,7 @@ struct dsdna_ctx {
   int64_t host_launches = 0;               // engine launches queued directly by the host
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   unsigned H = 0;
+  int table = TABLE_HASH;
   int morton_bits = 0;
   int nc[3] = {0, 0, 0};
   double cellh = 0;
@@ -300,7 +301,7 @@ static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
   a.spin_budget = 4000000000ull;
   a.X = c->X; a.V = c->V; a.Om = (Real*)c->Om; a.Kw = c->Kw; a.U = c->U; a.ud = c->ud;
   a.topo = c->topo; a.img = c->img; a.kref = c->kref; a.nbr = c->nbr; a.ncnt = c->ncnt;
-  a.cnt = c->cnt; a.start = c->start; a.H = c->H; a.morton_bits = c->morton_bits; a.key = c->key;
+  a.cnt = c->cnt; a.start = c->start; a.H = c->H; a.table = c->table; a.morton_bits = c->morton_bits; a.key = c->key;
   a.cent = c->cent; a.wpos = c->wpos; a.bsum = c->bsum;
   a.periodic = c->p.box[0] > 0.0 ? 1 : 0;
   for (int k = 0; k < 3; ++k) {
@@ -408,7 +409,9 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   const int64_t n = c->n;
   c->nseg = (n + c->T - 1) / c->T;
 
-  // cell table: Morton index of the wrapped cell in a periodic box, hash otherwise
+  // cell table: linear index of the wrapped cell in a periodic box with >= 3
+  // cells per edge (padded to whole 2048-entry scan tiles), Morton index in a
+  // smaller periodic box, hash of (molecule, cell) otherwise
   const double rc6 = std::pow(2.0, 1.0 / 6.0);
   const double rmax = rc6 * std::max(c->p.sigma_ss, c->p.sigma_cross) + c->p.skin + 0.01;
   c->cellh = rmax * 1.0001;
@@ -420,12 +423,21 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
       if (c->nc[k] > 1024) return bad(fail(c, DSDNA_EINVAL, "periodic box wider than 1024 cells"));
       while ((1 << bits) < c->nc[k]) ++bits;
     }
-    c->morton_bits = bits;
-    c->H = 1u << (3 * bits);    // one table entry per cell, in Morton order
+    if (c->nc[0] >= 3 && c->nc[1] >= 3 && c->nc[2] >= 3) {
+      const uint64_t cells = (uint64_t)c->nc[0] * c->nc[1] * c->nc[2];
+      c->H = (unsigned)((cells + 2047) / 2048 * 2048);
+      c->table = TABLE_LINEAR;
+      c->morton_bits = 0;
+    } else {
+      c->H = 1u << (3 * bits);    // one table entry per cell, in Morton order
+      c->table = TABLE_MORTON;
+      c->morton_bits = bits;
+    }
   } else {
     unsigned H = 1024;
     while ((int64_t)H < 2 * n) H <<= 1;
     c->H = H;
+    c->table = TABLE_HASH;
     c->morton_bits = 0;
   }
 

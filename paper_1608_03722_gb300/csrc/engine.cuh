@@ -23,6 +23,10 @@ namespace dsdna {
 
 // ---------------------------------------------------------------- constants
 enum : int { F_STERIC = 1, F_PREV = 2, F_NEXT = 4, F_FROZEN = 8, F_TOP = 16 };
+// Cell table: periodic box with >= 3 cells per edge -> linear index (x fastest;
+// the three x-neighbours of a cell are consecutive entries); smaller periodic
+// box -> Morton index; open box -> hash of (molecule, cell).
+enum : int { TABLE_HASH = 0, TABLE_MORTON = 1, TABLE_LINEAR = 2 };
 enum : unsigned {
   B_STALE = 1u, B_EFENE = 2u, B_ENAN = 4u, B_EOVF = 8u, B_ETIMEOUT = 16u, B_EIMG = 32u
 };
@@ -101,7 +105,8 @@ struct KArgs {
   unsigned* cnt;   // [H]
   unsigned* start; // [H + 1]
   unsigned H;
-  int morton_bits; // > 0: periodic Morton index with that many bits per axis
+  int table;       // TABLE_LINEAR, TABLE_MORTON or TABLE_HASH (cell_key)
+  int morton_bits; // TABLE_MORTON: bits per axis
   int* key;        // [n]
   float4* cent;    // [n] cell-sorted (position, slot)
   float4* wpos;    // [n] wrapped bead position, w = molecule

@@ -71,7 +71,8 @@ __device__ __forceinline__ unsigned spread3(unsigned v) {   // 10 bits -> every 
 
 template <class Real>
 __device__ __forceinline__ unsigned cell_key(const KArgs<Real>& a, int mol, int cx, int cy, int cz) {
-  if (a.morton_bits > 0) {   // periodic box: Morton index of the wrapped cell (no collisions)
+  if (a.table == TABLE_LINEAR) return (unsigned)cx + (unsigned)a.nc[0] * ((unsigned)cy + (unsigned)a.nc[1] * (unsigned)cz);
+  if (a.table == TABLE_MORTON) {   // small periodic box: Morton index of the wrapped cell (no collisions)
     return (spread3((unsigned)cx) | (spread3((unsigned)cy) << 1) | (spread3((unsigned)cz) << 2)) & (a.H - 1u);
   }
   unsigned h = (unsigned)cx * 0x8da6b343u ^ (unsigned)cy * 0xd8163841u ^ (unsigned)cz * 0xcb1ab31fu ^
@@ -279,7 +280,7 @@ __device__ void rebuild_scatter(const KArgs<Real>& a) {
 template <class Real, int CAPMAX>
 __device__ void list_one_bead(const KArgs<Real>& a, int64_t t, unsigned& fl) {
   const int JMASK = (1 << NBR_J_BITS) - 1;
-  const bool dedupe = !(a.morton_bits > 0 && a.nc[0] >= 3 && a.nc[1] >= 3 && a.nc[2] >= 3);
+  const bool dedupe = a.table != TABLE_LINEAR;
   {
     const float4 me = a.cent[t];
     const int gw = __float_as_int(me.w);
@@ -390,13 +391,15 @@ __device__ __forceinline__ void consider(const KArgs<Real>& a, const float* p, i
 // R4 (warp per table entry): the beads of one cell share one neighbourhood.
 // Lanes 0..26 read the ranges of the 27 neighbour cells at once, the warp
 // stages their beads in shared memory in tiles of LIST_TILE, and all 32 lanes
-// share the pair tests of up to LIST_CB beads of the cell against the tile;
-// hits go to per-bead shared buffers that the bead's lane sorts by partner
-// slot before writing its list.  Entries whose beads belong to several cells
-// (hash collisions) take the per-bead path.
+// share the (bead, candidate) pair tests of the cell against the tile.  Hits
+// go to per-bead shared buffers; a cell holds about three beads, so the warp
+// buffers the beads of consecutive cells and, once LIST_NB are waiting, one
+// lane per bead sorts its entries by partner slot and writes its list.
+// Entries whose beads belong to several cells (hash collisions) take the
+// per-bead path.
 constexpr int LIST_TILE = 128;
-constexpr int LIST_WARPS = 8;
-constexpr int LIST_CB = 16;
+constexpr int LIST_WARPS = 4;    // warps per CTA of the list kernel (static shared memory < 48 KB)
+constexpr int LIST_NB = 32;      // beads buffered per warp before their lists are sorted and written
 constexpr int LIST_CAP = 32;
 
 // typed pair test; returns the list entry (ent_make), or -1
@@ -427,17 +430,38 @@ __device__ __forceinline__ int pair_entry(const KArgs<Real>& a, float4 me, float
 template <class Real, int CAPMAX>
 __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
   __shared__ float4 tile[LIST_WARPS][LIST_TILE];
-  __shared__ int tent[LIST_WARPS][LIST_TILE];   // list entry of the staged candidate (image shift set)
-  __shared__ float4 cpos[LIST_WARPS][LIST_CB];
-  __shared__ int scount[LIST_WARPS][LIST_CB];
-  __shared__ int sent[LIST_WARPS][LIST_CB][LIST_CAP];
+  __shared__ float4 cpos[LIST_WARPS][LIST_NB];     // buffered beads (cell-sorted positions)
+  __shared__ int scount[LIST_WARPS][LIST_NB];
+  __shared__ int sent[LIST_WARPS][LIST_NB][LIST_CAP];
   __shared__ unsigned rb[LIST_WARPS][28], roff[LIST_WARPS][28];
-  __shared__ int rsh[LIST_WARPS][28];             // image shift of each neighbour cell (2-bit fields, x y z)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int JMASK = (1 << NBR_J_BITS) - 1;
-  const bool dedupe = !(a.morton_bits > 0 && a.nc[0] >= 3 && a.nc[1] >= 3 && a.nc[2] >= 3);
+  const bool dedupe = true;   // hash or small Morton table: a key may repeat among the 27
   const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
   const unsigned wid = blockIdx.x * (blockDim.x >> 5) + w;
+  int nb = 0;   // beads buffered by this warp (warp-uniform)
+  // one lane per buffered bead: order its entries by partner slot (the force
+  // sum order is then fixed) and write its list
+  auto flush = [&]() {
+    __syncwarp();
+    if (lane < nb) {
+      const int g = __float_as_int(cpos[w][lane].w) & JMASK;
+      const int total = scount[w][lane];
+      const int cnt = min(total, a.cap);
+      if (total > a.cap) fl |= B_EOVF;
+      int* e = sent[w][lane];
+      for (int x = 1; x < cnt; ++x) {
+        const int v = e[x];
+        int y = x;
+        while (y > 0 && (e[y - 1] & ENT_JMASK) > (v & ENT_JMASK)) { e[y] = e[y - 1]; --y; }
+        e[y] = v;
+      }
+      for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.n + g] = e[q];
+      a.ncnt[g] = cnt;
+    }
+    nb = 0;
+    __syncwarp();
+  };
   for (unsigned kb = wid * 32u; kb < a.H; kb += nwarps * 32u) {
     const unsigned k0 = kb + lane;
     const unsigned s0 = k0 < a.H ? a.start[k0] : 0u, s1 = k0 < a.H ? a.start[k0 + 1] : 0u;
@@ -449,7 +473,7 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
       int c0[3];
       int mol0 = 0;
       bool same = true;
-      if (a.morton_bits > 0 && a.n_mol == 1) {
+      if (a.table == TABLE_MORTON && a.n_mol == 1) {
         // one molecule in a periodic box: the table entry is exactly one cell
         const unsigned kc = kb + (unsigned)src;
         c0[0] = (int)compact3(kc); c0[1] = (int)compact3(kc >> 1); c0[2] = (int)compact3(kc >> 2);
@@ -480,14 +504,10 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
       }
       // ranges of the 27 neighbour cells, one per lane, duplicates (hash) dropped
       unsigned rbeg = 0, rlen = 0, key = 0xffffffffu;
-      int shift[3] = {0, 0, 0};   // image of the neighbour cell seen from this cell (periodic box)
       if (lane < 27) {
         int c3[3] = {c0[0] + (lane % 3) - 1, c0[1] + (lane / 3) % 3 - 1, c0[2] + lane / 9 - 1};
         if (a.periodic)
-          for (int c = 0; c < 3; ++c) {
-            shift[c] = c3[c] < 0 ? -1 : (c3[c] >= a.nc[c] ? 1 : 0);
-            c3[c] -= shift[c] * a.nc[c];
-          }
+          for (int c = 0; c < 3; ++c) c3[c] = c3[c] < 0 ? c3[c] + a.nc[c] : (c3[c] >= a.nc[c] ? c3[c] - a.nc[c] : c3[c]);
         key = cell_key(a, mol0, c3[0], c3[1], c3[2]);
       }
       if (dedupe) {
@@ -506,14 +526,12 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
         if (lane >= o) incl += y;
       }
       const unsigned M = __shfl_sync(0xffffffffu, incl, 31);
-      if (lane < 27) {
-        rb[w][lane] = rbeg; roff[w][lane] = incl - rlen;
-        rsh[w][lane] = ent_make(0, shift[0], shift[1], shift[2]);
-      }
+      if (lane < 27) { rb[w][lane] = rbeg; roff[w][lane] = incl - rlen; }
       __syncwarp();
-      for (unsigned cb = beg; cb < end; cb += LIST_CB) {
-        const int mc = (int)min((unsigned)LIST_CB, end - cb);
-        if (lane < mc) { cpos[w][lane] = a.cent[cb + lane]; scount[w][lane] = 0; }
+      for (unsigned cb = beg; cb < end;) {
+        const int mc = (int)min((unsigned)LIST_NB, end - cb);
+        if (nb + mc > LIST_NB) flush();
+        if (lane < mc) { cpos[w][nb + lane] = a.cent[cb + lane]; scount[w][nb + lane] = 0; }
         for (unsigned m0 = 0; m0 < M; m0 += LIST_TILE) {
           const unsigned mn = min((unsigned)LIST_TILE, M - m0);
           __syncwarp();
@@ -524,19 +542,7 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
               const int mid = (lo + hi + 1) >> 1;
               if (roff[w][mid] <= gi) lo = mid; else hi = mid - 1;
             }
-            float4 o = a.cent[rb[w][lo] + (gi - roff[w][lo])];
-            const int ej = __float_as_int(o.w) & JMASK;
-            int e = ej | rsh[w][lo];
-            if (!dedupe) {
-              // periodic Morton table with >= 3 cells per edge: every candidate of a
-              // neighbour cell takes that cell's image (the minimum image within rl)
-              o.x += (float)ent_shift(e, 0) * a.Lf[0];
-              o.y += (float)ent_shift(e, 1) * a.Lf[1];
-              o.z += (float)ent_shift(e, 2) * a.Lf[2];
-            }
-            if (a.n_mol > 1 && __float_as_int(a.wpos[ej].w) != mol0) e = -1;   // another molecule
-            tile[w][i] = o;
-            tent[w][i] = e;
+            tile[w][i] = a.cent[rb[w][lo] + (gi - roff[w][lo])];
           }
           __syncwarp();
           // (bead, candidate) pairs of this tile spread over the lanes
@@ -544,46 +550,100 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
           unsigned b = lane / mn, i = lane % mn;
           const unsigned qb = 32u / mn, qi = 32u % mn;
           for (unsigned pp = lane; pp < P; pp += 32) {
-            const float4 me = cpos[w][b];
-            int ent;
-            if (!dedupe) {
-              const float4 o = tile[w][i];
-              const int gw = __float_as_int(me.w), jw = __float_as_int(o.w);
-              const int g = gw & JMASK, j = jw & JMASK;
-              const float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
-              const float r2 = dx * dx + dy * dy + dz * dz;
-              const float rl2 = ((g ^ j) & 1) ? a.c.rl_cr2 : ((((gw & jw) >> NBR_J_BITS) & 1) ? a.c.rl_ss2 : -1.0f);
-              ent = (r2 < rl2 && j != g) ? tent[w][i] : -1;   // tent is -1 for another molecule
-            } else {
-              ent = pair_entry(a, me, tile[w][i], mol0);
-            }
+            const int ent = pair_entry(a, cpos[w][nb + b], tile[w][i], mol0);
             if (ent != -1) {
-              const int q = atomicAdd(&scount[w][b], 1);
-              if (q < LIST_CAP) sent[w][b][q] = ent;
+              const int q = atomicAdd(&scount[w][nb + b], 1);
+              if (q < LIST_CAP) sent[w][nb + b][q] = ent;
             }
             i += qi; b += qb;
             if (i >= mn) { i -= mn; ++b; }
           }
         }
-        __syncwarp();
-        if (lane < mc) {
-          const int g = __float_as_int(cpos[w][lane].w) & JMASK;
-          const int total = scount[w][lane];
-          const int cnt = min(total, a.cap);
-          if (total > a.cap) fl |= B_EOVF;
-          int* e = sent[w][lane];
-          for (int x = 1; x < cnt; ++x) {     // order by partner slot: the force sum order is fixed
-            const int v = e[x];
-            int y = x;
-            while (y > 0 && (e[y - 1] & ENT_JMASK) > (v & ENT_JMASK)) { e[y] = e[y - 1]; --y; }
-            e[y] = v;
-          }
-          for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.n + g] = e[q];
-          a.ncnt[g] = cnt;
-        }
-        __syncwarp();
+        nb += mc;
+        cb += mc;
       }
     }
+  }
+  flush();
+}
+
+// R4 for the linear table (periodic box, >= 3 cells per edge): one lane per
+// bead in cell order, so neighbouring lanes share most neighbour cells and
+// read them through L1.  A row of three x-consecutive cells is one range of
+// the sorted beads (two where the row wraps in x), so each bead walks at most
+// 18 (typically 9) ranges as one stream of candidates; every candidate of a
+// range takes the range's image, the minimum image within the list radius
+// because every edge has >= 3 cells of at least that radius.  Hits are
+// inserted in partner-slot order into the lane's buffer and then written.
+template <class Real>
+__device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl) {
+  __shared__ int sent[LIST_WARPS][32][LIST_CAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int JMASK = (1 << NBR_J_BITS) - 1;
+  int* list = sent[w][lane];
+  const int nx = a.nc[0], ny = a.nc[1], nz = a.nc[2];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
+    const float4 me = a.cent[t];
+    const int gw = __float_as_int(me.w), g = gw & JMASK;
+    const bool st_g = (gw >> NBR_J_BITS) & 1;
+    const int mol = a.n_mol > 1 ? __float_as_int(a.wpos[g].w) : 0;
+    const unsigned key = (unsigned)a.key[g];
+    const int cx = (int)(key % (unsigned)nx), cyz = (int)(key / (unsigned)nx);
+    const int cy = cyz % ny, cz = cyz / ny;
+    const int nparts = (cx == 0 || cx == nx - 1) ? 2 : 1;   // a row that wraps in x is two ranges
+    int cnt = 0, total = 0;
+    int row = 0, part = 0;
+    unsigned u = 0, e = 0;        // current candidate range [u, e) of the sorted beads
+    int sx = 0, sy = 0, sz = 0;   // its image
+    float ox = 0.f, oy = 0.f, oz = 0.f;
+    for (;;) {
+      while (u == e && row < 9) {
+        int y = cy + row % 3 - 1, z = cz + row / 3 - 1;
+        sy = y < 0 ? -1 : (y >= ny ? 1 : 0);
+        sz = z < 0 ? -1 : (z >= nz ? 1 : 0);
+        y -= sy * ny;
+        z -= sz * nz;
+        const unsigned rb = (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+        unsigned k0, k1;
+        if (cx == 0) {                 // cells nx-1 (image -1), then 0 and 1
+          k0 = part == 0 ? rb + nx - 1 : rb;
+          k1 = part == 0 ? rb + nx : rb + 2;
+          sx = part == 0 ? -1 : 0;
+        } else if (cx == nx - 1) {     // cells nx-2 and nx-1, then 0 (image +1)
+          k0 = part == 0 ? rb + nx - 2 : rb;
+          k1 = part == 0 ? rb + nx : rb + 1;
+          sx = part == 0 ? 0 : 1;
+        } else {
+          k0 = rb + cx - 1;
+          k1 = rb + cx + 2;
+          sx = 0;
+        }
+        u = a.start[k0];
+        e = a.start[k1];
+        ox = (float)sx * a.Lf[0];
+        oy = (float)sy * a.Lf[1];
+        oz = (float)sz * a.Lf[2];
+        if (++part == nparts) { part = 0; ++row; }
+      }
+      if (u == e) break;
+      const float4 o = a.cent[u++];
+      const int jw = __float_as_int(o.w), j = jw & JMASK;
+      const float dx = o.x + ox - me.x, dy = o.y + oy - me.y, dz = o.z + oz - me.z;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float rl2 = ((g ^ j) & 1) ? a.c.rl_cr2 : ((st_g && ((jw >> NBR_J_BITS) & 1)) ? a.c.rl_ss2 : -1.0f);
+      if (r2 < rl2 && j != g && (a.n_mol == 1 || __float_as_int(a.wpos[j].w) == mol)) {
+        ++total;
+        if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed
+          int q = cnt++;
+          while (q > 0 && (list[q - 1] & ENT_JMASK) > j) { list[q] = list[q - 1]; --q; }
+          list[q] = ent_make(j, sx, sy, sz);
+        }
+      }
+    }
+    if (total > a.cap) fl |= B_EOVF;
+    for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.n + g] = list[q];
+    a.ncnt[g] = cnt;
   }
 }
 
@@ -946,9 +1006,20 @@ __global__ void k_rebuild_scan_b(const KArgs<Real> a) {
 template <class Real>
 __global__ void k_rebuild_scatter(const KArgs<Real> a) { rebuild_scatter(a); }
 template <class Real, int CAPMAX>
-__global__ void __launch_bounds__(256) k_rebuild_list(const KArgs<Real> a) {
+__global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list(const KArgs<Real> a) {
   unsigned fl = 0;
   rebuild_list_warps<Real, CAPMAX>(a, fl);
+  if (fl) atomicOr(a.err, fl & B_ERRMASK);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.rebuild = 0;
+    *a.nrebuild += 1;
+  }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list_lanes(const KArgs<Real> a) {
+  unsigned fl = 0;
+  rebuild_list_lanes<Real>(a, fl);
   if (fl) atomicOr(a.err, fl & B_ERRMASK);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.rebuild = 0;

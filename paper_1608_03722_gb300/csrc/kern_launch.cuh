@@ -61,10 +61,20 @@ cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st)
   k_rebuild_scan_a<Real><<<scan_grid, T, 0, st>>>(a);
   k_rebuild_scan_b<Real><<<scan_grid, T, 0, st>>>(a);
   k_rebuild_scatter<Real><<<grid, T, 0, st>>>(a);
+  const int LT = LIST_WARPS * 32;
   int lbps = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lbps, k_rebuild_list<Real, CAPMAX>, T, 0);
-  const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.H + 255) / 256, (int64_t)nsm * std::max(1, lbps)));
-  k_rebuild_list<Real, CAPMAX><<<lgrid, T, 0, st>>>(a);
+  if (a.table == TABLE_LINEAR) {
+    // one lane per bead
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lbps, k_rebuild_list_lanes<Real>, LT, 0);
+    const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + LT - 1) / LT, (int64_t)nsm * std::max(1, lbps)));
+    k_rebuild_list_lanes<Real><<<lgrid, LT, 0, st>>>(a);
+  } else {
+    // one warp per 32 table entries at a time
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lbps, k_rebuild_list<Real, CAPMAX>, LT, 0);
+    const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.H + 32 * LT - 1) / (32 * LT),
+                                                                  (int64_t)nsm * std::max(1, lbps)));
+    k_rebuild_list<Real, CAPMAX><<<lgrid, LT, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -170,7 +170,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   const bool periodic = p->box[0] > 0.0;
   int nc[3] = {0, 0, 0};
   unsigned H = 1024;
-  int morton_bits = 0;
+  int morton_bits = 0, table = TABLE_HASH;
   if (periodic) {
     int bits = 1;
     for (int k = 0; k < 3; ++k) {
@@ -180,8 +180,14 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
       while ((1 << bits) < nc[k]) ++bits;
     }
     if (3 * bits > 15) return na_fail(DSDNA_EINVAL, "periodic box too wide for the fixed cell table (32 cells per edge)");
-    morton_bits = bits;
-    H = 1u << (3 * bits);
+    if (nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3) {
+      table = TABLE_LINEAR;
+      H = (unsigned)(((unsigned)nc[0] * nc[1] * nc[2] + 2047u) / 2048u * 2048u);
+    } else {
+      table = TABLE_MORTON;
+      morton_bits = bits;
+      H = 1u << (3 * bits);
+    }
   } else {
     while ((int64_t)H < 2 * n) H <<= 1;
   }
@@ -212,7 +218,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   a.ncnt = reinterpret_cast<int*>(b + O_NCNT);
   a.cnt = reinterpret_cast<unsigned*>(b + O_CNT);
   a.start = reinterpret_cast<unsigned*>(b + O_START);
-  a.H = H; a.morton_bits = morton_bits;
+  a.H = H; a.table = table; a.morton_bits = morton_bits;
   a.key = reinterpret_cast<int*>(b + O_KEY);
   a.cent = reinterpret_cast<float4*>(b + O_CENT);
   a.wpos = reinterpret_cast<float4*>(b + O_WPOS);

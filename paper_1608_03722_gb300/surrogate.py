@@ -252,12 +252,15 @@ def _broken_molecules(ctx, lengths, R0):
     return bad
 
 
-def _run_group(lengths, loads, kT, seed, steps, measure_from, every):
+def _run_group(lengths, loads, kT, seed, steps, measure_from, every, refine=1):
     """One context of tethered molecules at one kT; returns (labels, None) or
-    (None, indices of the molecules that broke) after a device error."""
+    (None, indices of the molecules that broke) after a device error.  With
+    refine = r the timestep is sweep_dt(kT) / r and every step count is
+    multiplied by r, so the samples fall at the same physical times."""
     from . import inputs as I
     cfg = I.ragged_batch(lengths, seed=seed)
-    p = D.dsdna_default_params(kT=float(kT), dt=sweep_dt(kT), seed=seed + 1000)
+    p = D.dsdna_default_params(kT=float(kT), dt=sweep_dt(kT) / refine, seed=seed + 1000)
+    steps, measure_from, every = steps * refine, measure_from * refine, every * refine
     ctx = D.Context(p, cfg.n_bp, X=cfg.X, u=cfg.u, tether=np.ones(len(lengths), np.int32))
     try:
         for m, (f, g) in enumerate(loads):
@@ -295,8 +298,10 @@ def simulate_sweep(points, steps: int = 4000, measure_from: int = 2000, every: i
     (chunked by size) at the timestep ``sweep_dt(kT)``.  The labels are the
     averages over the samples taken every ``every`` steps from
     ``measure_from`` on of: R_z / (0.34 (N-1)), (Tw - Tw0) / Tw0 and the
-    denatured fraction.  A molecule whose backbone breaks (FENE reaches R0)
-    gets NaN labels and its group is run again without it.
+    denatured fraction.  A molecule whose backbone breaks (FENE reaches R0,
+    an integration failure of the stiff bond under large loads) is taken out
+    of its group, which is run again without it, and is then simulated once
+    more at half the timestep; if it breaks again its labels are NaN.
     """
     pts = np.asarray(points, np.float64)
     out = np.zeros((len(pts), NO))
@@ -312,22 +317,35 @@ def simulate_sweep(points, steps: int = 4000, measure_from: int = 2000, every: i
             cur.append(i); tot += nt
         if cur:
             groups.append((kT, cur))
-    for gi, (kT, idx) in enumerate(groups):
-        idx = list(idx)
-        for _attempt in range(8):
-            if not idx:
-                break
-            lengths = [int(pts[i, 2]) for i in idx]
-            loads = [(pts[i, 0], pts[i, 1]) for i in idx]
-            lab, bad = _run_group(lengths, loads, kT, seed + gi, steps, measure_from, every)
-            if bad is None:
-                out[idx] = lab
-                break
-            for m in bad:
-                out[idx[m]] = np.nan
-            idx = [i for m, i in enumerate(idx) if m not in set(bad)]
-        else:
-            out[idx] = np.nan
+    def run(groups, refine):
+        broken = []
+        for gi, (kT, idx) in enumerate(groups):
+            idx = list(idx)
+            for _attempt in range(8):
+                if not idx:
+                    break
+                lengths = [int(pts[i, 2]) for i in idx]
+                loads = [(pts[i, 0], pts[i, 1]) for i in idx]
+                lab, bad = _run_group(lengths, loads, kT, seed + gi + 977 * (refine - 1), steps, measure_from, every,
+                                      refine)
+                if bad is None:
+                    out[idx] = lab
+                    break
+                for m in bad:
+                    out[idx[m]] = np.nan
+                    broken.append(idx[m])
+                idx = [i for m, i in enumerate(idx) if m not in set(bad)]
+            else:
+                out[idx] = np.nan
+                broken += idx
+        return broken
+
+    broken = run(groups, 1)
+    if broken:
+        again = {}
+        for i in broken:
+            again.setdefault(pts[i, 3], []).append(i)
+        run(sorted(again.items()), 2)
     return out
 
 
