@@ -42,6 +42,7 @@ struct dsdna_ctx {
   std::vector<int> tether;
   std::vector<double> ext;       // [n_mol][8]
   int64_t n = 0;
+  int64_t ns = 0;                // row stride of the [component][slot] arrays (n rounded up to 32)
   int maxN = 0;
   std::vector<void*> bufs;
   int64_t bytes = 0;
@@ -295,7 +296,7 @@ __attribute__((visibility("hidden"))) void fill_coef_mixed(const dsdna_params& p
 template <class Real>
 static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
   fill_coef(c->p, a.c);
-  a.n = c->n; a.n_mol = c->n_mol; a.nseg = (c->n + SEG_SLOTS - 1) / SEG_SLOTS; a.cap = c->p.max_neighbors;
+  a.n = c->n; a.ns = c->ns; a.n_mol = c->n_mol; a.nseg = (c->n + SEG_SLOTS - 1) / SEG_SLOTS; a.cap = c->p.max_neighbors;
   a.nsteps = 0; a.noise_mode = c->p.noise;
   a.seed_lo = (uint32_t)c->p.seed; a.seed_hi = (uint32_t)(c->p.seed >> 32);
   a.spin_budget = 4000000000ull;
@@ -358,7 +359,7 @@ static int upload_state(dsdna_ctx* c, int64_t g0, int64_t cnt, const double* X, 
     }
   CK(cudaMemcpyAsync(c->stage, h.data(), sizeof(double) * 12 * cnt, cudaMemcpyHostToDevice, c->st), "upload state");
   const int cur = (int)(c->step & 1);
-  k_scatter_state<<<(unsigned)((cnt + 255) / 256), 256, 0, c->st>>>(c->stage, g0, cnt, mask, c->fp64(), cur, c->n, c->X,
+  k_scatter_state<<<(unsigned)((cnt + 255) / 256), 256, 0, c->st>>>(c->stage, g0, cnt, mask, c->fp64(), cur, c->ns, c->X,
                                                                      c->V, c->Om, c->Kw, c->U, c->ud, c->topo);
   CK(cudaGetLastError(), "scatter state");
   CK(cudaStreamSynchronize(c->st), "upload state sync");
@@ -444,18 +445,20 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   // allocations
   const bool f64 = c->fp64();
   const size_t nn = (size_t)n;
+  c->ns = (n + 31) / 32 * 32;
+  const size_t ns = (size_t)c->ns;
 #define ALLOC(ptr, type, count)                                                              \
   do {                                                                                       \
     c->ptr = (type*)dalloc(c, sizeof(type) * (size_t)(count));                               \
     if (!c->ptr) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: " #ptr));       \
   } while (0)
-  ALLOC(X, double, (f64 ? 6 : 3) * nn);
-  ALLOC(V, double, 3 * nn);
-  c->Om = dalloc(c, (f64 ? 8 : 4) * 3 * nn);
+  ALLOC(X, double, (f64 ? 6 : 3) * ns);
+  ALLOC(V, double, 3 * ns);
+  c->Om = dalloc(c, (f64 ? 8 : 4) * 3 * ns);
   if (!c->Om) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: Om"));
-  if (f64) { ALLOC(ud, double, 6 * nn); } else { ALLOC(Kw, int4, 2 * nn); ALLOC(U, float4, 2 * nn); }
-  ALLOC(topo, int, nn); ALLOC(img, int, nn); ALLOC(kref, int, 3 * nn);
-  ALLOC(nbr, int, (size_t)c->p.max_neighbors * nn); ALLOC(ncnt, int, nn);
+  if (f64) { ALLOC(ud, double, 6 * ns); } else { ALLOC(Kw, int4, 2 * ns); ALLOC(U, float4, 2 * ns); }
+  ALLOC(topo, int, ns); ALLOC(img, int, ns); ALLOC(kref, int, 3 * ns);
+  ALLOC(nbr, int, (size_t)c->p.max_neighbors * ns); ALLOC(ncnt, int, ns);
   ALLOC(cnt, unsigned, c->H); ALLOC(start, unsigned, (size_t)c->H + 1); ALLOC(key, int, nn);
   ALLOC(cent, float4, nn); ALLOC(wpos, float4, nn);
   ALLOC(mol_off, int64_t, c->n_mol + 1); ALLOC(ext_d, double, (size_t)c->n_mol * 8);
@@ -485,7 +488,7 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   if (!c->bsum) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: bsum"));
 
   // topology flags (Sec. 2; anchored and loaded base pairs of Sec. 4)
-  std::vector<int> topo(nn);
+  std::vector<int> topo(ns, 0);   // padding slots: no flags
   for (int m = 0; m < c->n_mol; ++m) {
     const int N = c->n_bp[m];
     for (int k = 0; k < N; ++k)
@@ -502,17 +505,22 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
       }
   }
   auto cpy = [&](void* dst, const void* src, size_t b) { return cudaMemcpy(dst, src, b, cudaMemcpyHostToDevice); };
-  if (cpy(c->topo, topo.data(), sizeof(int) * nn) != cudaSuccess ||
+  if (cpy(c->topo, topo.data(), sizeof(int) * ns) != cudaSuccess ||
       cpy(c->mol_off, c->off.data(), sizeof(int64_t) * (c->n_mol + 1)) != cudaSuccess ||
       cpy(c->ext_d, c->ext.data(), sizeof(double) * c->ext.size()) != cudaSuccess)
     return bad(fail(c, DSDNA_ECUDA, "topology upload"));
   if (cudaMemset(c->cnt, 0, sizeof(unsigned) * c->H) != cudaSuccess || cudaMemset(c->err, 0, 16) != cudaSuccess ||
       cudaMemset(c->step_d, 0, 8) != cudaSuccess || cudaMemset(c->nrebuild, 0, 8) != cudaSuccess ||
       cudaMemset(c->nlaunch, 0, 8) != cudaSuccess ||
-      cudaMemset(c->bar, 0, sizeof(GridBar)) != cudaSuccess || cudaMemset(c->ncnt, 0, sizeof(int) * nn) != cudaSuccess ||
-      cudaMemset(c->Om, 0, (f64 ? 8 : 4) * 3 * nn) != cudaSuccess || cudaMemset(c->V, 0, 24 * nn) != cudaSuccess)
+      cudaMemset(c->bar, 0, sizeof(GridBar)) != cudaSuccess || cudaMemset(c->ncnt, 0, sizeof(int) * ns) != cudaSuccess ||
+      cudaMemset(c->Om, 0, (f64 ? 8 : 4) * 3 * ns) != cudaSuccess || cudaMemset(c->V, 0, 24 * ns) != cudaSuccess ||
+      cudaMemset(c->X, 0, (f64 ? 48 : 24) * ns) != cudaSuccess || cudaMemset(c->kref, 0, 12 * ns) != cudaSuccess ||
+      cudaMemset(c->img, 0, 4 * ns) != cudaSuccess)
     return bad(fail(c, DSDNA_ECUDA, "initialisation"));
-  if (!f64 && cudaMemset(c->Kw, 0, sizeof(int4) * 2 * nn) != cudaSuccess) return bad(fail(c, DSDNA_ECUDA, "initialisation"));
+  if (!f64 && (cudaMemset(c->Kw, 0, sizeof(int4) * 2 * ns) != cudaSuccess ||
+               cudaMemset(c->U, 0, sizeof(float4) * 2 * ns) != cudaSuccess))
+    return bad(fail(c, DSDNA_ECUDA, "initialisation"));
+  if (f64 && cudaMemset(c->ud, 0, 48 * ns) != cudaSuccess) return bad(fail(c, DSDNA_ECUDA, "initialisation"));
   const int one = 1;
   if (cpy(c->rebuild, &one, sizeof(int)) != cudaSuccess) return bad(fail(c, DSDNA_ECUDA, "initialisation"));
   fill_args(c, c->kf);
@@ -829,10 +837,10 @@ extern "C" int dsdna_observables(dsdna_ctx* c, int mol, unsigned flags, dsdna_ob
   if (rc) return rc;
   const int cur = (int)(c->step & 1);
   ObsArgs a{};
-  a.n = c->n;
-  a.X = c->fp64() ? c->X + (size_t)cur * 3 * c->n : c->X;
-  a.uf = c->fp64() ? nullptr : c->U + (size_t)cur * c->n;
-  a.ud = c->fp64() ? c->ud + (size_t)cur * 3 * c->n : nullptr;
+  a.n = c->ns;   // row stride of the [3][n] arrays
+  a.X = c->fp64() ? c->X + (size_t)cur * 3 * c->ns : c->X;
+  a.uf = c->fp64() ? nullptr : c->U + (size_t)cur * c->ns;
+  a.ud = c->fp64() ? c->ud + (size_t)cur * 3 * c->ns : nullptr;
   a.g0 = 2 * c->off[mol];
   a.N = c->n_bp[mol];
   a.h = 0.5 * c->p.ell;
@@ -868,7 +876,7 @@ extern "C" int dsdna_get_state(dsdna_ctx* c, int mol, double* X, double* V, doub
   const int64_t g0 = mol < 0 ? 0 : 2 * c->off[mol];
   const int64_t cnt = mol < 0 ? c->n : 2 * (int64_t)c->n_bp[mol];
   const int cur = (int)(c->step & 1);
-  k_gather_state<<<(unsigned)((cnt + 255) / 256), 256, 0, c->st>>>(c->stage, g0, cnt, c->fp64(), cur, c->n, c->X, c->V,
+  k_gather_state<<<(unsigned)((cnt + 255) / 256), 256, 0, c->st>>>(c->stage, g0, cnt, c->fp64(), cur, c->ns, c->X, c->V,
                                                                     c->Om, c->U, c->ud);
   CK(cudaGetLastError(), "gather state");
   std::vector<double> h((size_t)cnt * 12);
@@ -923,14 +931,14 @@ extern "C" int dsdna_neighbor_pairs(dsdna_ctx* c, int64_t cap, int64_t* pi, int6
   if (rc) return rc;
   rc = sync_check(c);
   if (rc) return rc;
-  const size_t nn = (size_t)c->n;
-  std::vector<int> nb((size_t)c->p.max_neighbors * nn), nc(nn);
+  const size_t nn = (size_t)c->n, ns = (size_t)c->ns;
+  std::vector<int> nb((size_t)c->p.max_neighbors * ns), nc(nn);
   CK(cudaMemcpy(nb.data(), c->nbr, sizeof(int) * nb.size(), cudaMemcpyDeviceToHost), "read list");
   CK(cudaMemcpy(nc.data(), c->ncnt, sizeof(int) * nc.size(), cudaMemcpyDeviceToHost), "read counts");
   int64_t k = 0;
   for (size_t i = 0; i < nn; ++i)
     for (int q = 0; q < nc[i]; ++q) {
-      const int64_t j = nb[(size_t)q * nn + i] & ENT_JMASK;
+      const int64_t j = nb[(size_t)q * ns + i] & ENT_JMASK;
       if ((int64_t)i < j) {
         if (k < cap) { pi[k] = (int64_t)i; pj[k] = j; }
         ++k;

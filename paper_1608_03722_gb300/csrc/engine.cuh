@@ -82,6 +82,7 @@ template <class Real>
 struct KArgs {
   Coef<Real> c;
   int64_t n;
+  int64_t ns;      // row stride of the [component][slot] arrays: n rounded up to a multiple of 32
   int n_mol;
   int64_t nseg;
   int cap;
@@ -90,6 +91,7 @@ struct KArgs {
   uint32_t seed_lo, seed_hi;
   unsigned long long spin_budget;
   // state
+  // [k][n] below means k rows of ns entries (slots n .. ns-1 are padding)
   double* X;       // mixed: [3][n]; fp64: [2][3][n]
   double* V;       // [3][n]
   Real* Om;        // [3][n]
@@ -99,7 +101,7 @@ struct KArgs {
   const int* topo; // [n] flags | mol << 8
   int* img;        // [n] packed image (both modes)
   int* kref;       // [3][n] mirror at the last build
-  int* nbr;        // [cap][n] (j | image code << 27)
+  int* nbr;        // [cap][n] list entries (ent_make)
   int* ncnt;       // [n]
   // cell hash
   unsigned* cnt;   // [H]
@@ -284,15 +286,15 @@ __device__ __forceinline__ int bead_off(float hu) { return __float2int_rn(-hu * 
 template <class Real>
 __device__ __forceinline__ void load_slot(const KArgs<Real>& a, int cur, int64_t g, SPos<Real>& s) {
   if constexpr (sizeof(Real) == 4) {
-    const int4 k = a.Kw[(size_t)cur * a.n + g];
-    const float4 u = a.U[(size_t)cur * a.n + g];
+    const int4 k = a.Kw[(size_t)cur * a.ns + g];
+    const float4 u = a.U[(size_t)cur * a.ns + g];
     s.kx = k.x; s.ky = k.y; s.kz = k.z;
     s.ux = u.x; s.uy = u.y; s.uz = u.z;
   } else {
-    const double* X = a.X + (size_t)cur * 3 * a.n;
-    const double* u = a.ud + (size_t)cur * 3 * a.n;
-    s.x = X[g]; s.y = X[a.n + g]; s.z = X[2 * a.n + g];
-    s.ux = u[g]; s.uy = u[a.n + g]; s.uz = u[2 * a.n + g];
+    const double* X = a.X + (size_t)cur * 3 * a.ns;
+    const double* u = a.ud + (size_t)cur * 3 * a.ns;
+    s.x = X[g]; s.y = X[a.ns + g]; s.z = X[2 * a.ns + g];
+    s.ux = u[g]; s.uy = u[a.ns + g]; s.uz = u[2 * a.ns + g];
   }
 }
 

@@ -85,14 +85,14 @@ template <class Real>
 __device__ __forceinline__ void bead_position_f(const KArgs<Real>& a, int cur, int64_t g, float* b) {
   const float h = (float)a.c.h;
   if constexpr (sizeof(Real) == 4) {
-    const float4 u = a.U[(size_t)cur * a.n + g];
+    const float4 u = a.U[(size_t)cur * a.ns + g];
     b[0] = d2f_bits(a.X[g]) - h * u.x;
-    b[1] = d2f_bits(a.X[a.n + g]) - h * u.y;
-    b[2] = d2f_bits(a.X[2 * a.n + g]) - h * u.z;
+    b[1] = d2f_bits(a.X[a.ns + g]) - h * u.y;
+    b[2] = d2f_bits(a.X[2 * a.ns + g]) - h * u.z;
   } else {
-    const double* X = a.X + (size_t)cur * 3 * a.n;
-    const double* u = a.ud + (size_t)cur * 3 * a.n;
-    for (int c = 0; c < 3; ++c) b[c] = (float)(X[c * a.n + g] - (double)h * u[c * a.n + g]);
+    const double* X = a.X + (size_t)cur * 3 * a.ns;
+    const double* u = a.ud + (size_t)cur * 3 * a.ns;
+    for (int c = 0; c < 3; ++c) b[c] = (float)(X[c * a.ns + g] - (double)h * u[c * a.ns + g]);
   }
 }
 
@@ -100,14 +100,14 @@ template <class Real>
 __device__ __forceinline__ void bead_position(const KArgs<Real>& a, int cur, int64_t g, double* b) {
   const double h = (double)a.c.h;
   if constexpr (sizeof(Real) == 4) {
-    const float4 u = a.U[(size_t)cur * a.n + g];
+    const float4 u = a.U[(size_t)cur * a.ns + g];
     b[0] = a.X[g] - h * (double)u.x;
-    b[1] = a.X[a.n + g] - h * (double)u.y;
-    b[2] = a.X[2 * a.n + g] - h * (double)u.z;
+    b[1] = a.X[a.ns + g] - h * (double)u.y;
+    b[2] = a.X[2 * a.ns + g] - h * (double)u.z;
   } else {
-    const double* X = a.X + (size_t)cur * 3 * a.n;
-    const double* u = a.ud + (size_t)cur * 3 * a.n;
-    for (int c = 0; c < 3; ++c) b[c] = X[c * a.n + g] - h * u[c * a.n + g];
+    const double* X = a.X + (size_t)cur * 3 * a.ns;
+    const double* u = a.ud + (size_t)cur * 3 * a.ns;
+    for (int c = 0; c < 3; ++c) b[c] = X[c * a.ns + g] - h * u[c * a.ns + g];
   }
 }
 
@@ -148,17 +148,17 @@ __device__ void rebuild_bin(const KArgs<Real>& a, int cur, unsigned& fl) {
     // build-time bead position on the fixed-point grid, for the rebuild trigger
     const float h = (float)a.c.h;
     if constexpr (sizeof(Real) == 4) {
-      int4 kw = a.Kw[(size_t)cur * a.n + g];
-      const float4 u = a.U[(size_t)cur * a.n + g];
+      int4 kw = a.Kw[(size_t)cur * a.ns + g];
+      const float4 u = a.U[(size_t)cur * a.ns + g];
       a.kref[g] = kw.x + bead_off(h * u.x);
-      a.kref[a.n + g] = kw.y + bead_off(h * u.y);
-      a.kref[2 * a.n + g] = kw.z + bead_off(h * u.z);
+      a.kref[a.ns + g] = kw.y + bead_off(h * u.y);
+      a.kref[2 * a.ns + g] = kw.z + bead_off(h * u.z);
       kw.w = packed;
-      a.Kw[(size_t)cur * a.n + g] = kw;
+      a.Kw[(size_t)cur * a.ns + g] = kw;
     } else {
-      const double* X = a.X + (size_t)cur * 3 * a.n;
-      const double* u = a.ud + (size_t)cur * 3 * a.n;
-      for (int c = 0; c < 3; ++c) a.kref[c * a.n + g] = fix32(X[c * a.n + g]) + bead_off(h * (float)u[c * a.n + g]);
+      const double* X = a.X + (size_t)cur * 3 * a.ns;
+      const double* u = a.ud + (size_t)cur * 3 * a.ns;
+      for (int c = 0; c < 3; ++c) a.kref[c * a.ns + g] = fix32(X[c * a.ns + g]) + bead_off(h * (float)u[c * a.ns + g]);
     }
   }
 }
@@ -351,7 +351,7 @@ __device__ void list_one_bead(const KArgs<Real>& a, int64_t t, unsigned& fl) {
       }
     }
     if (total > a.cap) fl |= B_EOVF;
-    for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.n + g] = list[q];
+    for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.ns + g] = list[q];
     a.ncnt[g] = cnt;
   }
 }
@@ -456,7 +456,7 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
         while (y > 0 && (e[y - 1] & ENT_JMASK) > (v & ENT_JMASK)) { e[y] = e[y - 1]; --y; }
         e[y] = v;
       }
-      for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.n + g] = e[q];
+      for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.ns + g] = e[q];
       a.ncnt[g] = cnt;
     }
     nb = 0;
@@ -642,7 +642,7 @@ __device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl) {
       }
     }
     if (total > a.cap) fl |= B_EOVF;
-    for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.n + g] = list[q];
+    for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.ns + g] = list[q];
     a.ncnt[g] = cnt;
   }
 }
@@ -743,13 +743,13 @@ template <class Real>
 __device__ __forceinline__ void store_state(const KArgs<Real>& a, int nxt, int64_t g, int k0, int k1, int k2,
                                             const double* X, V3<Real> u, int packed) {
   if constexpr (sizeof(Real) == 4) {
-    a.Kw[(size_t)nxt * a.n + g] = make_int4(k0, k1, k2, packed);
-    a.U[(size_t)nxt * a.n + g] = make_float4(u.x, u.y, u.z, 0.0f);
+    a.Kw[(size_t)nxt * a.ns + g] = make_int4(k0, k1, k2, packed);
+    a.U[(size_t)nxt * a.ns + g] = make_float4(u.x, u.y, u.z, 0.0f);
   } else {
-    double* Xo = a.X + (size_t)nxt * 3 * a.n;
-    double* uo = a.ud + (size_t)nxt * 3 * a.n;
-    Xo[g] = X[0]; Xo[a.n + g] = X[1]; Xo[2 * a.n + g] = X[2];
-    uo[g] = u.x; uo[a.n + g] = u.y; uo[2 * a.n + g] = u.z;
+    double* Xo = a.X + (size_t)nxt * 3 * a.ns;
+    double* uo = a.ud + (size_t)nxt * 3 * a.ns;
+    Xo[g] = X[0]; Xo[a.ns + g] = X[1]; Xo[2 * a.ns + g] = X[2];
+    uo[g] = u.x; uo[a.ns + g] = u.y; uo[2 * a.ns + g] = u.z;
   }
 }
 
@@ -808,13 +808,13 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       const int nn = a.ncnt[g];
       const int img_me = a.periodic ? a.img[g] : 0;
       for (int q = 0; q < nn; ++q) {
-        const int ent = a.nbr[(size_t)q * a.n + g];
+        const int ent = a.nbr[(size_t)q * a.ns + g];
         const int j = ent & ENT_JMASK;
         V3<Real> R;
         V3<Real> uj;
         if constexpr (sizeof(Real) == 4) {
-          const int4 kj = a.Kw[(size_t)cur * a.n + j];
-          const float4 u4 = a.U[(size_t)cur * a.n + j];
+          const int4 kj = a.Kw[(size_t)cur * a.ns + j];
+          const float4 u4 = a.U[(size_t)cur * a.ns + j];
           uj = V3<float>{u4.x, u4.y, u4.z};
           unsigned dx = (unsigned)kj.x - (unsigned)me.kx, dy = (unsigned)kj.y - (unsigned)me.ky,
                    dz = (unsigned)kj.z - (unsigned)me.kz;
@@ -826,10 +826,10 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
           }
           R = V3<float>{(float)(int)dx * FIX_SCALE_F, (float)(int)dy * FIX_SCALE_F, (float)(int)dz * FIX_SCALE_F};
         } else {
-          const double* X = a.X + (size_t)cur * 3 * a.n;
-          const double* ud = a.ud + (size_t)cur * 3 * a.n;
-          uj = V3<double>{ud[j], ud[a.n + j], ud[2 * a.n + j]};
-          R = V3<double>{X[j] - me.x, X[a.n + j] - me.y, X[2 * a.n + j] - me.z};
+          const double* X = a.X + (size_t)cur * 3 * a.ns;
+          const double* ud = a.ud + (size_t)cur * 3 * a.ns;
+          uj = V3<double>{ud[j], ud[a.ns + j], ud[2 * a.ns + j]};
+          R = V3<double>{X[j] - me.x, X[a.ns + j] - me.y, X[2 * a.ns + j] - me.z};
           if (a.periodic) {
             const int ij = a.img[j];
             R.x += (double)(img_comp(img_me, 0) - img_comp(ij, 0) + ent_shift(ent, 0)) * a.L[0];
@@ -877,12 +877,12 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       const uint32_t local = (uint32_t)(g - 2 * a.mol_off[mol]);
       double Xd[3], Vd[3];
       if constexpr (sizeof(Real) == 4) {
-        Xd[0] = a.X[g]; Xd[1] = a.X[a.n + g]; Xd[2] = a.X[2 * a.n + g];
+        Xd[0] = a.X[g]; Xd[1] = a.X[a.ns + g]; Xd[2] = a.X[2 * a.ns + g];
       } else {
         Xd[0] = me.x; Xd[1] = me.y; Xd[2] = me.z;
       }
-      Vd[0] = a.V[g]; Vd[1] = a.V[a.n + g]; Vd[2] = a.V[2 * a.n + g];
-      V3<Real> Om{a.Om[g], a.Om[a.n + g], a.Om[2 * a.n + g]};
+      Vd[0] = a.V[g]; Vd[1] = a.V[a.ns + g]; Vd[2] = a.V[2 * a.ns + g];
+      V3<Real> Om{a.Om[g], a.Om[a.ns + g], a.Om[2 * a.ns + g]};
       const bool frozen = (f & F_FROZEN) != 0;
       V3<Real> Ft{0, 0, 0}, Tt{0, 0, 0};
       if (!frozen) {
@@ -934,21 +934,21 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
           if (!(isfinite(Ft.x) && isfinite(Ft.y) && isfinite(Ft.z) && isfinite(Om.x) && isfinite(Om.y) &&
                 isfinite(Om.z)))
             fl |= B_ENAN;
-          a.V[g] = Vd[0]; a.V[a.n + g] = Vd[1]; a.V[2 * a.n + g] = Vd[2];
-          a.Om[g] = Om.x; a.Om[a.n + g] = Om.y; a.Om[2 * a.n + g] = Om.z;
+          a.V[g] = Vd[0]; a.V[a.ns + g] = Vd[1]; a.V[2 * a.ns + g] = Vd[2];
+          a.Om[g] = Om.x; a.Om[a.ns + g] = Om.y; a.Om[2 * a.ns + g] = Om.z;
           if constexpr (sizeof(Real) == 4) {
-            a.X[g] = Xd[0]; a.X[a.n + g] = Xd[1]; a.X[2 * a.n + g] = Xd[2];
+            a.X[g] = Xd[0]; a.X[a.ns + g] = Xd[1]; a.X[2 * a.ns + g] = Xd[2];
           }
         }
         int packed = 0;
-        if constexpr (sizeof(Real) == 4) packed = a.Kw[(size_t)cur * a.n + g].w;
+        if constexpr (sizeof(Real) == 4) packed = a.Kw[(size_t)cur * a.ns + g].w;
         const int k0 = fix32(Xd[0]), k1 = fix32(Xd[1]), k2 = fix32(Xd[2]);
         store_state(a, nxt, g, k0, k1, k2, Xd, un, packed);
         // rebuild trigger: a bead moved more than skin/2 since the last build
         const float hf = (float)h;
         const float ddx = fixdiff(a.kref[g], k0 + bead_off(hf * (float)un.x));
-        const float ddy = fixdiff(a.kref[a.n + g], k1 + bead_off(hf * (float)un.y));
-        const float ddz = fixdiff(a.kref[2 * a.n + g], k2 + bead_off(hf * (float)un.z));
+        const float ddy = fixdiff(a.kref[a.ns + g], k1 + bead_off(hf * (float)un.y));
+        const float ddz = fixdiff(a.kref[2 * a.ns + g], k2 + bead_off(hf * (float)un.z));
         if (ddx * ddx + ddy * ddy + ddz * ddz > a.c.skin_half2) fl |= B_STALE;
       }
     }

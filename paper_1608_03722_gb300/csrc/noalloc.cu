@@ -105,7 +105,7 @@ int setup_device(int dev, DeviceSetup** out) {
 // Stage the caller's configuration into the scratch array: topology flags of
 // Sec. 2 (no anchored or loaded base pairs), SoA centres, fixed-point mirror,
 // FP32 orientation; zero the cell counts' companions and the control words.
-__global__ void k_noalloc_prep(const double* X, const double* u, int64_t n, int n_mol, const int64_t* mol_off,
+__global__ void k_noalloc_prep(const double* X, const double* u, int64_t n, int64_t ns, int n_mol, const int64_t* mol_off,
                                int steric_phase, double* Xs, int4* Kw, float4* U, int* topo, unsigned* ctrl) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g == 0) {
@@ -132,7 +132,7 @@ __global__ void k_noalloc_prep(const double* X, const double* u, int64_t n, int 
   if (q < N - 1) f |= F_NEXT;
   topo[g] = f | (m << 8);
   const double x0 = X[3 * g], x1 = X[3 * g + 1], x2 = X[3 * g + 2];
-  Xs[g] = x0; Xs[n + g] = x1; Xs[2 * n + g] = x2;
+  Xs[g] = x0; Xs[ns + g] = x1; Xs[2 * ns + g] = x2;
   Kw[g] = make_int4(fix32(x0), fix32(x1), fix32(x2), 0);
   double u0 = u[3 * g], u1 = u[3 * g + 1], u2 = u[3 * g + 2];
   const double l2 = u0 * u0 + u1 * u1 + u2 * u2;
@@ -203,7 +203,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
 
   KArgs<float> a{};
   fill_coef_mixed(*p, a.c);
-  a.n = n; a.n_mol = n_mol; a.nseg = (n + 31) / 32; a.cap = NA_CAP;
+  a.n = n; a.ns = NA_MAX_NT; a.n_mol = n_mol; a.nseg = (n + 31) / 32; a.cap = NA_CAP;
   a.nsteps = 0; a.noise_mode = 0; a.seed_lo = 0; a.seed_hi = 0;
   a.spin_budget = 4000000000ull;
   a.X = reinterpret_cast<double*>(b + O_X);
@@ -251,7 +251,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   if (e == cudaSuccess) e = cudaMemsetAsync(a.bar, 0, sizeof(GridBar), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.ncnt, 0, sizeof(int) * n, st);
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
-  k_noalloc_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, u, n, n_mol, a.mol_off, p->steric_phase, a.X, a.Kw, a.U,
+  k_noalloc_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, u, n, NA_MAX_NT, n_mol, a.mol_off, p->steric_phase, a.X, a.Kw, a.U,
                                                                const_cast<int*>(a.topo), ctrl);
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));

@@ -9,7 +9,7 @@ struct ObsArgs {
   const double* X;    // [3][n] centres (FP64)
   const float4* uf;   // [n] orientation (mixed precision) or nullptr
   const double* ud;   // [3][n] orientation (FP64) when uf == nullptr
-  int64_t n;          // nucleotides in the system
+  int64_t n;          // row stride of the [3][n] arrays (nucleotides rounded up to 32)
   int64_t g0;         // first slot of the molecule
   int N;              // base pairs of the molecule
   double h;           // ell / 2
