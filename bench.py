@@ -371,20 +371,22 @@ def main():
                       "K x md_steps steps run right after the timed region",
             "kernel": "engine_kernel<float,STEP> (fused forces + Langevin, persistent cooperative)"}
 
-    # end to end through the C ABI with host buffers: upload state, step, download state
+    # end to end through the C ABI with pinned host buffers: upload the state
+    # (X, V, u, Omega), step, download the state, every bench step
     e2e = None
     if not args.no_e2e and rank == 0:
-        X, V, u, Om = ctx.get_state()
+        host = tuple(torch.empty((cfg.n_nt, 3), dtype=torch.float64, pin_memory=True).numpy() for _ in range(4))
+        ctx.get_state(out=host)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         n_e2e = max(1, min(K, 3))
         for _ in range(n_e2e):
-            ctx.set_state(-1, X, V, u, Om)
+            ctx.set_state(-1, *host)
             ctx.step(S)
-            X, V, u, Om = ctx.get_state()
+            ctx.get_state(out=host)
         dt_e2e = time.perf_counter() - t0
         e2e = {"value": cfg.n_nt * S * n_e2e / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * 3 * 8 * cfg.n_nt,
-               "d2h_bytes_per_step": 4 * 3 * 8 * cfg.n_nt, "steps": n_e2e}
+               "d2h_bytes_per_step": 4 * 3 * 8 * cfg.n_nt, "steps": n_e2e, "host_buffers": "pinned"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -196,13 +196,16 @@ static void host_maxwell(const dsdna_params& p, int mol, int N, const double* u,
 }
 
 // ---------------------------------------------------------------- state transfer kernels
-// staging layout: [n][12] = X xyz, V xyz, u xyz, Om xyz (AoS, FP64)
-__global__ void k_scatter_state(double* stage, int64_t g0, int64_t cnt, unsigned mask, int fp64, int cur, int64_t n,
+// staging layout: four [cnt][3] FP64 regions X, V, u, Om -- the callers' own
+// layout, so each array moves in one copy
+__global__ void k_scatter_state(const double* stage, int64_t g0, int64_t cnt, unsigned mask, int fp64, int cur, int64_t n,
                                 double* X, double* V, void* Om, int4* Kw, float4* U, double* ud, const int* topo) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cnt) return;
   const int64_t g = g0 + i;
-  const double* s = stage + 12 * i;
+  double s[12];
+  for (int r = 0; r < 4; ++r)
+    for (int q = 0; q < 3; ++q) s[3 * r + q] = stage[3 * (r * cnt + i) + q];
   double* Xc = fp64 ? X + (size_t)cur * 3 * n : X;
   const bool frozen = (topo[g] & F_FROZEN) != 0;
   if (mask & 1) for (int c = 0; c < 3; ++c) Xc[c * n + g] = s[c];
@@ -240,7 +243,7 @@ __global__ void k_gather_state(double* stage, int64_t g0, int64_t cnt, int fp64,
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cnt) return;
   const int64_t g = g0 + i;
-  double* s = stage + 12 * i;
+  double s[12];
   const double* Xc = fp64 ? X + (size_t)cur * 3 * n : X;
   for (int c = 0; c < 3; ++c) { s[c] = Xc[c * n + g]; s[3 + c] = V[c * n + g]; }
   if (fp64) {
@@ -251,6 +254,8 @@ __global__ void k_gather_state(double* stage, int64_t g0, int64_t cnt, int fp64,
     s[6] = u.x; s[7] = u.y; s[8] = u.z;
     for (int c = 0; c < 3; ++c) s[9 + c] = ((const float*)Om)[c * n + g];
   }
+  for (int r = 0; r < 4; ++r)
+    for (int q = 0; q < 3; ++q) stage[3 * (r * cnt + i) + q] = s[3 * r + q];
 }
 
 // ---------------------------------------------------------------- setup
@@ -349,15 +354,11 @@ static int upload_state(dsdna_ctx* c, int64_t g0, int64_t cnt, const double* X, 
                         const double* Om) {
   unsigned mask = (X ? 1u : 0u) | (V ? 2u : 0u) | (u ? 4u : 0u) | (Om ? 8u : 0u);
   if (!mask || cnt == 0) return DSDNA_OK;
-  std::vector<double> h((size_t)cnt * 12, 0.0);
-  for (int64_t i = 0; i < cnt; ++i)
-    for (int q = 0; q < 3; ++q) {
-      if (X) h[12 * i + q] = X[3 * i + q];
-      if (V) h[12 * i + 3 + q] = V[3 * i + q];
-      if (u) h[12 * i + 6 + q] = u[3 * i + q];
-      if (Om) h[12 * i + 9 + q] = Om[3 * i + q];
-    }
-  CK(cudaMemcpyAsync(c->stage, h.data(), sizeof(double) * 12 * cnt, cudaMemcpyHostToDevice, c->st), "upload state");
+  const double* src[4] = {X, V, u, Om};
+  for (int r = 0; r < 4; ++r)
+    if (src[r])
+      CK(cudaMemcpyAsync(c->stage + 3 * r * cnt, src[r], sizeof(double) * 3 * cnt, cudaMemcpyHostToDevice, c->st),
+         "upload state");
   const int cur = (int)(c->step & 1);
   k_scatter_state<<<(unsigned)((cnt + 255) / 256), 256, 0, c->st>>>(c->stage, g0, cnt, mask, c->fp64(), cur, c->ns, c->X,
                                                                      c->V, c->Om, c->Kw, c->U, c->ud, c->topo);
@@ -879,16 +880,12 @@ extern "C" int dsdna_get_state(dsdna_ctx* c, int mol, double* X, double* V, doub
   k_gather_state<<<(unsigned)((cnt + 255) / 256), 256, 0, c->st>>>(c->stage, g0, cnt, c->fp64(), cur, c->ns, c->X, c->V,
                                                                     c->Om, c->U, c->ud);
   CK(cudaGetLastError(), "gather state");
-  std::vector<double> h((size_t)cnt * 12);
-  CK(cudaMemcpyAsync(h.data(), c->stage, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st), "download state");
+  double* dst[4] = {X, V, u, Om};
+  for (int r = 0; r < 4; ++r)
+    if (dst[r])
+      CK(cudaMemcpyAsync(dst[r], c->stage + 3 * r * cnt, sizeof(double) * 3 * cnt, cudaMemcpyDeviceToHost, c->st),
+         "download state");
   CK(cudaStreamSynchronize(c->st), "download sync");
-  for (int64_t i = 0; i < cnt; ++i)
-    for (int q = 0; q < 3; ++q) {
-      if (X) X[3 * i + q] = h[12 * i + q];
-      if (V) V[3 * i + q] = h[12 * i + 3 + q];
-      if (u) u[3 * i + q] = h[12 * i + 6 + q];
-      if (Om) Om[3 * i + q] = h[12 * i + 9 + q];
-    }
   return DSDNA_OK;
 }
 

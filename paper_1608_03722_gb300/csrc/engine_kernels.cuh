@@ -709,10 +709,13 @@ __device__ __forceinline__ void flush_energy(const KArgs<Real>& a, int mol, Real
   for (int k = 0; k < 6; ++k) if (W[k] != (Real)0) atomicAdd(dst + NTERMS + k, (double)W[k]);
 }
 
-// Stage slot g into its ring entry (f = 0 for a slot outside [0, n)).  Loading
-// the next tile's slots one tile ahead in registers was measured slower: at
-// 64 registers it spills, and at 80 registers three CTAs per SM hide less
-// latency than four.
+// Stage slot g into its ring entry (f = 0 for a slot outside [0, n)).  Two
+// ways of loading ahead were measured slower: the next tile's slots in
+// registers (64 registers spill; at 80 registers three CTAs per SM hide less
+// latency than four), and cp.async copies of each lane's list data and of its
+// first two partners into shared memory one tile ahead (the 3 KB per warp of
+// buffers cut residency from 32 to 24 warps per SM: 159 against 136 us per
+// step at 1 Mbp).
 template <class Real>
 __device__ __forceinline__ void stage_slot(const KArgs<Real>& a, const SegSmem<Real>& sm, int cur, int64_t g) {
   const int ri = ring(g);
