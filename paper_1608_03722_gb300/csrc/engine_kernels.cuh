@@ -591,45 +591,66 @@ __device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl) {
     const unsigned key = (unsigned)a.key[g];
     const int cx = (int)(key % (unsigned)nx), cyz = (int)(key / (unsigned)nx);
     const int cy = cyz % ny, cz = cyz / ny;
-    const int nparts = (cx == 0 || cx == nx - 1) ? 2 : 1;   // a row that wraps in x is two ranges
-    int cnt = 0, total = 0;
-    int row = 0, part = 0;
-    unsigned u = 0, e = 0;        // current candidate range [u, e) of the sorted beads
-    int sx = 0, sy = 0, sz = 0;   // its image
-    float ox = 0.f, oy = 0.f, oz = 0.f;
-    for (;;) {
-      while (u == e && row < 9) {
-        int y = cy + row % 3 - 1, z = cz + row / 3 - 1;
-        sy = y < 0 ? -1 : (y >= ny ? 1 : 0);
-        sz = z < 0 ? -1 : (z >= nz ? 1 : 0);
-        y -= sy * ny;
-        z -= sz * nz;
-        const unsigned rb = (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
-        unsigned k0, k1;
-        if (cx == 0) {                 // cells nx-1 (image -1), then 0 and 1
-          k0 = part == 0 ? rb + nx - 1 : rb;
-          k1 = part == 0 ? rb + nx : rb + 2;
-          sx = part == 0 ? -1 : 0;
-        } else if (cx == nx - 1) {     // cells nx-2 and nx-1, then 0 (image +1)
-          k0 = part == 0 ? rb + nx - 2 : rb;
-          k1 = part == 0 ? rb + nx : rb + 1;
-          sx = part == 0 ? 0 : 1;
-        } else {
-          k0 = rb + cx - 1;
-          k1 = rb + cx + 2;
-          sx = 0;
-        }
-        u = a.start[k0];
-        e = a.start[k1];
-        ox = (float)sx * a.Lf[0];
-        oy = (float)sy * a.Lf[1];
-        oz = (float)sz * a.Lf[2];
-        if (++part == nparts) { part = 0; ++row; }
+    // candidate ranges: 9 rows (dy, dz) of three x-consecutive cells, a row
+    // that wraps in x split in two; range i holds the cells [k0, k1) and its
+    // image as ent_make(0, sx, sy, sz)
+    const int nparts = (cx == 0 || cx == nx - 1) ? 2 : 1;
+    const int nr = 9 * nparts;
+    auto range = [&](int i, unsigned& k0, unsigned& k1, int& code) {
+      const int row = nparts == 2 ? (i >> 1) : i, part = nparts == 2 ? (i & 1) : 0;
+      int y = cy + row % 3 - 1, z = cz + row / 3 - 1;
+      const int sy = y < 0 ? -1 : (y >= ny ? 1 : 0);
+      const int sz = z < 0 ? -1 : (z >= nz ? 1 : 0);
+      y -= sy * ny;
+      z -= sz * nz;
+      const unsigned rb = (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
+      int sx = 0;
+      if (cx == 0) {                 // cells nx-1 (image -1), then 0 and 1
+        k0 = part == 0 ? rb + nx - 1 : rb;
+        k1 = part == 0 ? rb + nx : rb + 2;
+        sx = part == 0 ? -1 : 0;
+      } else if (cx == nx - 1) {     // cells nx-2 and nx-1, then 0 (image +1)
+        k0 = part == 0 ? rb + nx - 2 : rb;
+        k1 = part == 0 ? rb + nx : rb + 1;
+        sx = part == 0 ? 0 : 1;
+      } else {
+        k0 = rb + cx - 1;
+        k1 = rb + cx + 2;
       }
-      if (u == e) break;
+      code = ent_make(0, sx, sy, sz);
+    };
+    int cnt = 0, total = 0;
+    unsigned k0, k1;
+    int code, ncode = 0;
+    range(0, k0, k1, code);
+    unsigned u = a.start[k0], e = a.start[k1], nu = 0, ne = 0;
+    int i = 1;
+    if (i < nr) {   // the next range's bounds load while this range is walked
+      range(i, k0, k1, ncode);
+      nu = a.start[k0];
+      ne = a.start[k1];
+    }
+    // the bead moved by minus the range's image: candidates are compared as stored
+    float px = me.x - (float)ent_shift(code, 0) * a.Lf[0];
+    float py = me.y - (float)ent_shift(code, 1) * a.Lf[1];
+    float pz = me.z - (float)ent_shift(code, 2) * a.Lf[2];
+    for (;;) {
+      if (u == e) {
+        if (i >= nr) break;
+        u = nu; e = ne; code = ncode;
+        if (++i < nr) {
+          range(i, k0, k1, ncode);
+          nu = a.start[k0];
+          ne = a.start[k1];
+        }
+        px = me.x - (float)ent_shift(code, 0) * a.Lf[0];
+        py = me.y - (float)ent_shift(code, 1) * a.Lf[1];
+        pz = me.z - (float)ent_shift(code, 2) * a.Lf[2];
+        continue;
+      }
       const float4 o = a.cent[u++];
       const int jw = __float_as_int(o.w), j = jw & JMASK;
-      const float dx = o.x + ox - me.x, dy = o.y + oy - me.y, dz = o.z + oz - me.z;
+      const float dx = o.x - px, dy = o.y - py, dz = o.z - pz;
       const float r2 = dx * dx + dy * dy + dz * dz;
       const float rl2 = ((g ^ j) & 1) ? a.c.rl_cr2 : ((st_g && ((jw >> NBR_J_BITS) & 1)) ? a.c.rl_ss2 : -1.0f);
       if (r2 < rl2 && j != g && (a.n_mol == 1 || __float_as_int(a.wpos[j].w) == mol)) {
@@ -637,7 +658,7 @@ __device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl) {
         if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed
           int q = cnt++;
           while (q > 0 && (list[q - 1] & ENT_JMASK) > j) { list[q] = list[q - 1]; --q; }
-          list[q] = ent_make(j, sx, sy, sz);
+          list[q] = j | code;
         }
       }
     }

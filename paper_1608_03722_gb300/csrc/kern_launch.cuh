@@ -69,9 +69,10 @@ cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st)
     const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + LT - 1) / LT, (int64_t)nsm * std::max(1, lbps)));
     k_rebuild_list_lanes<Real><<<lgrid, LT, 0, st>>>(a);
   } else {
-    // one warp per 32 table entries at a time
+    // one warp per 32 table entries at a time: enough CTAs for every chunk of
+    // a small table, at most a full wave for a large one
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lbps, k_rebuild_list<Real, CAPMAX>, LT, 0);
-    const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.H + 32 * LT - 1) / (32 * LT),
+    const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)a.H + 32 * LIST_WARPS - 1) / (32 * LIST_WARPS),
                                                                   (int64_t)nsm * std::max(1, lbps)));
     k_rebuild_list<Real, CAPMAX><<<lgrid, LT, 0, st>>>(a);
   }
