@@ -51,6 +51,9 @@ def build_workload(name: str, seed: int = 0, n_bp: int = 1_000_000):
     elif name == "c4":
         cfg = I.c4_batch(seed=seed)
         desc = f"256 independent molecules, lengths log-uniform 500-20000 bp ({cfg.n_nt} nucleotides)"
+    elif name == "paper960":
+        cfg = I.paper_array(40, 40, 600, seed=seed)
+        desc = "paper benchmark geometry: 40x40 array of 600 bp strands (960 kbp, 1,920,000 nucleotides), periodic"
     elif name == "c1":
         cfg = I.c1_linear(200, seed=seed)
         desc = "linear dsDNA, 200 bp = 400 nucleotides, open boundaries"
@@ -222,6 +225,35 @@ def compare_batched(D, torch, n_mol=256, steps=100, fp64_sample=16, fp64_steps=5
             "speedup": batched / fp64}
 
 
+# Paper's time unit: tau_Br = 2.28e-9 s and dt = 0.005 tau_Br (App. A), so
+# simulated milliseconds per wall-clock day = steps/s * dt * 86400 s * 1e3.
+MS_PER_DAY_PER_STEP_S = 0.005 * 2.28e-9 * 86400.0 * 1e3
+# The paper's strong-scaling figures on ARCHER (Cray XC30, 24-core Ivy Bridge nodes), Sec. 6 / Fig. 11.
+PAPER_FIG11 = {"10x10": "about 2 ms/day on 512 cores",
+               "40x40": "about 0.4 ms/day on 2048 cores, up to 1 ms/day on 8192 cores"}
+
+
+def compare_paper(D, torch, steps=100, reps=5):
+    """The paper's benchmark geometry (regular arrays of 600 bp strands) run
+    through the batched engine; simulated time per wall-clock day beside the
+    paper's Fig. 11 figures."""
+    from paper_1608_03722_gb300 import inputs as I
+    out = {}
+    for nx in (10, 40):
+        cfg = I.paper_array(nx, nx, 600)
+        p = D.dsdna_default_params(box=cfg.box, skin=0.3)
+        ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om)
+        t = timed_steps(ctx, torch, steps, reps)
+        ctx.close()
+        steps_s = steps * reps / t
+        key = f"{nx}x{nx}"
+        out[key] = {"workload": f"{nx}x{nx} array of 600 bp strands ({cfg.n_nt} nucleotides), periodic box "
+                                f"{cfg.box[0]:.0f}x{cfg.box[1]:.0f}x{cfg.box[2]:.0f} nm",
+                    "value": cfg.n_nt * steps_s, "unit": UNIT, "steps_per_s": steps_s,
+                    "ms_per_day": steps_s * MS_PER_DAY_PER_STEP_S, "paper": PAPER_FIG11[key]}
+    return out
+
+
 def reference_arm(args, ws, rank):
     if rank != 0:
         return 0
@@ -248,7 +280,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "paper960"])
     ap.add_argument("--md-steps", type=int, default=100)
     ap.add_argument("--n-bp", type=int, default=1_000_000, help="base pairs of the confined workload")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -398,6 +430,7 @@ def main():
     compare = None
     if rank == 0 and not args.no_compare:
         compare = compare_batched(D, torch)
+        compare["paper_benchmark"] = compare_paper(D, torch)
         from paper_1608_03722_gb300 import surrogate as SUR
         st = SUR.run_sweep_study(n_train=256, n_test=64, n_query=32, length=(100, 400), steps=8000,
                                  measure_from=2000, every=100, iters=3000)

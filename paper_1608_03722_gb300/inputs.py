@@ -341,6 +341,27 @@ def c4_batch(n_mol: int = 256, lo: int = 500, hi: int = 20_000, seed: int = 0) -
                   ext_f=ext_f, ext_t=ext_t)
 
 
+def paper_array(nx: int = 40, ny: int = 40, n_bp: int = 600, spacing: float = 5.0, seed: int = 0) -> Config:
+    """The paper's benchmark geometry (Sec. 6): a regular nx x ny array of
+    linear n_bp dsDNA strands (40 x 40 x 600 bp = 960 kbp, 1.92e6 nucleotides;
+    10 x 10 = 60 kbp).  The paper gives no spacing or box; here the relaxed
+    helices stand along z on a square lattice of `spacing` nm in a periodic box
+    of nx*spacing x ny*spacing x (n_bp*0.34 + spacing) nm, random start phases."""
+    rng = np.random.default_rng(seed)
+    Xs, us = [], []
+    for ix in range(nx):
+        for iy in range(ny):
+            axis, d = helix_frame(n_bp, ((ix + 0.5) * spacing, (iy + 0.5) * spacing, 0.5 * spacing), (0, 0, 1), (1, 0, 0),
+                                  phase0=rng.uniform(0.0, 2.0 * math.pi))
+            X, u = place(axis, d)
+            Xs.append(X); us.append(u)
+    X = np.concatenate(Xs); u = np.concatenate(us)
+    n = np.full(nx * ny, n_bp, np.int32)
+    V, Om = maxwell(u, rng)
+    box = (nx * spacing, ny * spacing, n_bp * RISE + spacing)
+    return Config("paper_array_%dx%dx%dbp" % (nx, ny, n_bp), n, X, u, V, Om, box=box)
+
+
 def ragged_batch(lengths, seed: int = 0, spread: float = 0.0) -> Config:
     """Molecules of the given lengths, optionally jittered, for parity tests."""
     rng = np.random.default_rng(seed)

@@ -39,6 +39,32 @@ def test_batch_forces_equal_each_molecule_alone(prec):
         assert np.array_equal(fb, Fb[sl]) and np.array_equal(fp, Fp[sl]), m
 
 
+def test_periodic_array_molecules_equal_alone_and_oracle():
+    """Paper's benchmark geometry in small (3 x 3 strands of 40 bp, periodic box,
+    linear cell table with >= 3 cells per edge): each molecule's forces in the
+    array equal its forces alone in the same box bit for bit, and the array's
+    forces match the FP64 oracle."""
+    cfg = I.paper_array(3, 3, 40, spacing=5.0, seed=2)
+    X, u = I.perturb(cfg.X, cfg.u, np.random.default_rng(3), dx=0.02, dtheta=0.05)
+    p = D.dsdna_default_params(box=cfg.box)
+    ctx = D.Context(p, cfg.n_bp, X=X, V=cfg.V, u=u, Om=cfg.Om)
+    Fb, Fp = ctx.compute_forces()
+    Xs, _, us, _ = ctx.get_state()
+    ctx.close()
+    off = np.concatenate([[0], np.cumsum(cfg.n_bp)])
+    for m in range(len(cfg.n_bp)):
+        sl = slice(2 * off[m], 2 * off[m + 1])
+        c1 = D.Context(p, [int(cfg.n_bp[m])], X=X[sl], V=cfg.V[sl], u=u[sl], Om=cfg.Om[sl])
+        fb, fp = c1.compute_forces()
+        c1.close()
+        assert np.array_equal(fb, Fb[sl]) and np.array_equal(fp, Fp[sl]), m
+    po = O.params(box=cfg.box)
+    r = O.forces(po, cfg.n_bp, Xs, us, cells=True)
+    Sb, Sp = O.force_scale(po, cfg.n_bp, Xs, us)
+    for Fg, Fo, Sc in ((Fb, r["Fb"], Sb), (Fp, r["Fp"], Sp)):
+        assert (np.linalg.norm(Fg - Fo, axis=1) / (1e-5 * Sc + 5e-4)).max() < 1.0
+
+
 def test_autotune_picks_a_candidate_and_keeps_the_forces():
     cfg = I.ragged_batch([130, 1, 64, 257, 2, 33, 500], seed=4)   # relaxed helices: the trials run dynamics
     p0 = D.dsdna_default_params()
