@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "engine_kernels.cuh"
+#include "rebuild.cuh"
 
 namespace dsdna {
 
