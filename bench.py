@@ -39,6 +39,16 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(dist, x: float, device) -> float:
+    """Largest x over all ranks of the process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def build_workload(name: str, seed: int = 0, n_bp: int = 1_000_000):
     from paper_1608_03722_gb300 import inputs as I
     if name == "c3":
@@ -350,10 +360,7 @@ def main():
     ctx.synchronize()
     ms = e0.elapsed_time(e1)
     info1 = ctx.info()
-    t_local = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
+    ms_max = max_over_ranks(dist, ms, "cuda")
     nt_steps = cfg.n_nt * S * K * ws
     value = nt_steps / (ms_max * 1e-3)
 
