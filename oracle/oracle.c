@@ -55,6 +55,7 @@ void or_default_params(or_params* p) {
   /* App. A: kT = 1, gamma = 1 in simulation units, dt = 0.005 tau_Br (Eq. 16) */
   p->kT = 1.0; p->gamma = 1.0; p->dt = 0.005;
   p->seed = 0; p->noise = 1; p->steric_phase = 0;
+  p->bubble_rule = 0; p->K2_gc = 0.0; p->gc = NULL;
   p->box[0] = p->box[1] = p->box[2] = 0.0;
 }
 
@@ -175,13 +176,13 @@ static void term_morse(const or_params* p, const double* d, double* e, double* f
 
 /* App. A Eq. 10: truncated harmonic hydrogen bond between paired patches;
  * zero (broken) beyond rc, tested on r^2 <= rc^2. */
-static void term_hbond(const or_params* p, const double* d, double* e, double* f) {
+static void term_hbond(const or_params* p, double K2, const double* d, double* e, double* f) {
   double r2 = v_dot(d, d);
   f[0] = f[1] = f[2] = 0.0; *e = 0.0;
   if (r2 > p->rc_hb * p->rc_hb) return;
   double r = sqrt(r2);
   double w = p->r0_hb - p->rc_hb;
-  double k = p->K2 / (2.0 * w * w);
+  double k = K2 / (2.0 * w * w);
   *e = k * ((r - p->r0_hb) * (r - p->r0_hb) - (p->rc_hb - p->r0_hb) * (p->rc_hb - p->r0_hb));
   /* -(dU/dr)/r = -2k (r - r0)/r = -2k (1 - r0/r) */
   double fr = (p->r0_hb == 0.0) ? -2.0 * k : ((r > 0.0) ? -2.0 * k * (r - p->r0_hb) / r : 0.0);
@@ -298,11 +299,33 @@ static void tout_add(tout_t* o, int64_t slot, int site, const double* f, const d
   o->vir[3] += rel[0] * f[1]; o->vir[4] += rel[0] * f[2]; o->vir[5] += rel[1] * f[2];
 }
 
+/* Sec. 5: a base pair is open (denatured) when its hydrogen bond is broken,
+ * r^2 > rc^2 between the paired patches; a base pair outside molecule m
+ * counts as closed. */
+static int bp_open(const or_params* p, const topo_t* t, const double* X, const double* u, int m, int64_t bp) {
+  if (bp < t->off[m] || bp >= t->off[m] + t->n_bp[m]) return 0;
+  double pa[3], pb[3], d[3];
+  site_pos(p, X, u, 2 * bp, 1, pa);
+  site_pos(p, X, u, 2 * bp + 1, 1, pb);
+  disp(p, pa, pb, d);
+  return v_dot(d, d) > p->rc_hb * p->rc_hb;
+}
+
+/* Hydrogen-bond stiffness of base pair bp (Sec. 5: K2(AT) < K2(CG)). */
+static double pair_K2(const or_params* p, int64_t bp) {
+  if (p->gc && p->gc[bp] && p->K2_gc > 0.0) return p->K2_gc;
+  return p->K2;
+}
+
 /* All bonded terms owned by nucleotide g (everything that starts at g along
- * its strand in 5'->3' order, plus the bending term centred on g). */
+ * its strand in 5'->3' order, plus the bending term centred on g).  With the
+ * bubble rule of Sec. 5 the dihedral of the step g -> n is left out when both
+ * base pairs lie in a run of at least three consecutive open base pairs, and
+ * the bending at g when its three base pairs are all open. */
 static int owner_terms(const or_params* p, const topo_t* t, const double* X, const double* u, int64_t g, tout_t* o) {
   static const double zero[3] = {0, 0, 0};
   int64_t n = next_nt(t, g), pv = prev_nt(t, g);
+  const int m = mol_of(t, g);
   double bg[3], pg[3];
   site_pos(p, X, u, g, 0, bg);
   site_pos(p, X, u, g, 1, pg);
@@ -326,10 +349,18 @@ static int owner_terms(const or_params* p, const topo_t* t, const double* X, con
     tout_add(o, g, 1, mf, zero); tout_add(o, n, 1, f, d);
     /* dihedral A-E-F-B = b_g, p_g, p_n, b_n; positions relative to A */
     double rE[3], rF[3], rB[3], fA[3], fE[3], fF[3], fB[3];
-    disp(p, bg, pg, rE); disp(p, bg, pn, rF); disp(p, bg, bn, rB);
-    term_dihedral(p, rE, rF, rB, &e1, fA, fE, fF, fB, NULL);
-    o->e[OR_E_DIHEDRAL] += e1;
-    tout_add(o, g, 0, fA, zero); tout_add(o, g, 1, fE, rE); tout_add(o, n, 1, fF, rF); tout_add(o, n, 0, fB, rB);
+    int in_bubble = 0;
+    if (p->bubble_rule) {
+      const int64_t kg = g / 2, kn = n / 2, lo = kg < kn ? kg : kn, hi = kg < kn ? kn : kg;
+      in_bubble = bp_open(p, t, X, u, m, kg) && bp_open(p, t, X, u, m, kn) &&
+                  (bp_open(p, t, X, u, m, lo - 1) || bp_open(p, t, X, u, m, hi + 1));
+    }
+    if (!in_bubble) {
+      disp(p, bg, pg, rE); disp(p, bg, pn, rF); disp(p, bg, bn, rB);
+      term_dihedral(p, rE, rF, rB, &e1, fA, fE, fF, fB, NULL);
+      o->e[OR_E_DIHEDRAL] += e1;
+      tout_add(o, g, 0, fA, zero); tout_add(o, g, 1, fE, rE); tout_add(o, n, 1, fF, rF); tout_add(o, n, 0, fB, rB);
+    }
     /* planarity: angle at p_n between p_g and b_n; positions relative to p_g */
     double v1[3], v2[3], rpn[3], rbn[3];
     disp(p, pn, pg, v1); disp(p, pn, bn, v2);
@@ -338,7 +369,8 @@ static int owner_terms(const or_params* p, const topo_t* t, const double* X, con
     disp(p, pg, pn, rpn); disp(p, pg, bn, rbn);
     tout_add(o, g, 1, fE, zero); tout_add(o, n, 1, fF, rpn); tout_add(o, n, 0, fB, rbn);
   }
-  if (n >= 0 && pv >= 0) {
+  if (n >= 0 && pv >= 0 &&
+      !(p->bubble_rule && bp_open(p, t, X, u, m, pv / 2) && bp_open(p, t, X, u, m, g / 2) && bp_open(p, t, X, u, m, n / 2))) {
     double pp[3], pn[3], v1[3], v2[3], f1[3], fv[3], f2[3], e1, r1[3], r2[3];
     site_pos(p, X, u, pv, 1, pp);
     site_pos(p, X, u, n, 1, pn);
@@ -358,7 +390,7 @@ static void hbond_terms(const or_params* p, const double* X, const double* u, in
   site_pos(p, X, u, g, 1, pa);
   site_pos(p, X, u, g + 1, 1, pb);
   disp(p, pa, pb, d);
-  term_hbond(p, d, &e, f);
+  term_hbond(p, pair_K2(p, g / 2), d, &e, f);
   o->e[OR_E_HBOND] += e;
   mf[0] = -f[0]; mf[1] = -f[1]; mf[2] = -f[2];
   tout_add(o, g, 1, mf, zero); tout_add(o, g + 1, 1, f, d);

@@ -65,6 +65,10 @@ typedef struct {
   int noise;                           /* 0 off, 1 uniform (variance matched), 2 Gaussian */
   int steric_phase;                    /* steric iff (index along strand) % 3 == phase */
   double box[3];                       /* > 0: periodic edge; <= 0: open */
+  /* Sec. 5 denaturation */
+  int bubble_rule;                     /* 1: no dihedral / bending inside bubbles of > 2 open base pairs */
+  double K2_gc;                        /* hydrogen-bond stiffness of G.C pairs (<= 0: K2) */
+  const signed char* gc;               /* per base pair over all molecules: 1 = G.C, 0 = A.T (NULL: all K2) */
 } or_params;
 
 void or_default_params(or_params* p);
