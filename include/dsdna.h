@@ -21,6 +21,9 @@
  *   - Observables: extension R_z (Sec. 4.1), twist from base-pair frames
  *     (Sec. 3.2, App. B), linking number by the Gauss integral of the closed
  *     strands (App. C Eq. 17), denatured fraction (Sec. 5).
+ *   - Denaturation (Sec. 5): per-pair hydrogen-bond stiffness (A.T / G.C) and
+ *     the bubble rule that drops dihedral and bending terms inside runs of
+ *     more than two open base pairs (dsdna_params.bubble_rule, K2_gc).
  *
  * Layout of host arrays: AoS, X[3*g + c], with nucleotide slot
  * g = 2*(bp_offset(mol) + k) + s; s = 0 is strand A nucleotide k, s = 1 its
@@ -114,6 +117,15 @@ typedef struct dsdna_params {
   int block_threads;                     /* threads per CTA of the step kernel (0: default 256; 64..256, multiple of 32) */
   int blocks_per_sm;                     /* persistent CTAs per SM (0: as many as fit) */
   int steps_per_graph;                   /* steps per captured CUDA graph launch (0: default 50) */
+  /* Sec. 5 denaturation.  A base pair is open when its hydrogen bond is
+   * broken (patch distance > rc_hb).  With bubble_rule = 1 the dihedral of a
+   * strand step is left out when both of its base pairs lie in a run of at
+   * least three consecutive open base pairs, and the bending angle at a
+   * nucleotide when the base pairs of it and of its two strand neighbours are
+   * all open.  K2_gc is the hydrogen-bond stiffness of base pairs flagged G.C
+   * in dsdna_system.gc (<= 0: K2 for every pair). */
+  int bubble_rule;                       /* 0 or 1 */
+  double K2_gc;
 } dsdna_params;
 
 /* Molecules and (optional) initial state.  NULL X/u builds ideal relaxed
@@ -128,6 +140,7 @@ typedef struct dsdna_system {
   const double* u;       /* [3*n_nt] or NULL (with X) */
   const double* Om;      /* [3*n_nt] or NULL (with V) */
   const int* tether;     /* [n_mol] or NULL */
+  const signed char* gc; /* [n_bp total] 1 = G.C pair (stiffness K2_gc), 0 = A.T (K2), or NULL: all A.T */
 } dsdna_system;
 
 /* Device allocator used for every buffer of a context.  NULL: cudaMalloc/cudaFree. */

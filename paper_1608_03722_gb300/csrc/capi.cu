@@ -266,6 +266,7 @@ static void fill_coef(const dsdna_params& p, Coef<Real>& c) {
   c.K1 = (Real)p.K1; c.R02 = (Real)(p.R0 * p.R0); c.eps_bb = (Real)p.eps_bb;
   c.sbb2 = (Real)(p.sigma_bb * p.sigma_bb); c.rcbb2 = (Real)(rc6 * rc6 * p.sigma_bb * p.sigma_bb);
   c.khb = (Real)(p.K2 / (2.0 * (p.r0_hb - p.rc_hb) * (p.r0_hb - p.rc_hb)));
+  c.khb_gc = (Real)((p.K2_gc > 0.0 ? p.K2_gc : p.K2) / (2.0 * (p.r0_hb - p.rc_hb) * (p.r0_hb - p.rc_hb)));
   c.r0hb = (Real)p.r0_hb; c.rchb2 = (Real)(p.rc_hb * p.rc_hb);
   c.eps = (Real)p.eps_ev;
   c.sss2 = (Real)(p.sigma_ss * p.sigma_ss); c.rcss2 = (Real)(rc6 * rc6 * p.sigma_ss * p.sigma_ss);
@@ -303,6 +304,7 @@ static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
   fill_coef(c->p, a.c);
   a.n = c->n; a.ns = c->ns; a.n_mol = c->n_mol; a.nseg = (c->n + SEG_SLOTS - 1) / SEG_SLOTS; a.cap = c->p.max_neighbors;
   a.nsteps = 0; a.noise_mode = c->p.noise;
+  a.bubble = c->p.bubble_rule ? 1 : 0;
   a.seed_lo = (uint32_t)c->p.seed; a.seed_hi = (uint32_t)(c->p.seed >> 32);
   a.spin_budget = 4000000000ull;
   a.X = c->X; a.V = c->V; a.Om = (Real*)c->Om; a.Kw = c->Kw; a.U = c->U; a.ud = c->ud;
@@ -340,6 +342,8 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
   if (!(p->dt > 0.0) || !(p->mass > 0.0) || !(p->ell > 0.0) || !(p->R0 > 0.0) || !(p->rc_hb > 0.0) || p->gamma < 0.0 || p->kT < 0.0)
     return fail(nullptr, DSDNA_EINVAL, "non-positive dt/mass/ell/R0/rc or negative gamma/kT");
   if (p->precision != DSDNA_PREC_MIXED && p->precision != DSDNA_PREC_FP64) return fail(nullptr, DSDNA_EINVAL, "precision");
+  if (p->bubble_rule != 0 && p->bubble_rule != 1) return fail(nullptr, DSDNA_EINVAL, "bubble_rule must be 0 or 1");
+  if (p->K2_gc < 0.0) return fail(nullptr, DSDNA_EINVAL, "K2_gc must be >= 0");
   if (p->noise < 0 || p->noise > 2) return fail(nullptr, DSDNA_EINVAL, "noise mode");
   if (p->skin < 0.0 || p->skin > 1.0) return fail(nullptr, DSDNA_EINVAL, "skin must be in [0, 1] nm");
   if (p->max_neighbors < 0 || p->max_neighbors > 32) return fail(nullptr, DSDNA_EINVAL, "max_neighbors must be <= 32");
@@ -502,6 +506,7 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
         if (q < N - 1) f |= F_NEXT;
         if (c->tether[m] && k == 0) f |= F_FROZEN;
         if (k == N - 1) f |= F_TOP;
+        if (sys->gc && sys->gc[c->off[m] + k]) f |= F_GC;   // Sec. 5: G.C pair, stiffer hydrogen bond
         topo[g] = f | (m << 8);
       }
   }

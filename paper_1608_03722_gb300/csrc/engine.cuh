@@ -22,7 +22,7 @@
 namespace dsdna {
 
 // ---------------------------------------------------------------- constants
-enum : int { F_STERIC = 1, F_PREV = 2, F_NEXT = 4, F_FROZEN = 8, F_TOP = 16 };
+enum : int { F_STERIC = 1, F_PREV = 2, F_NEXT = 4, F_FROZEN = 8, F_TOP = 16, F_GC = 32 };
 // Cell table: periodic box with >= 3 cells per edge -> linear index (x fastest;
 // the three x-neighbours of a cell are consecutive entries); smaller periodic
 // box -> Morton index; open box -> hash of (molecule, cell).
@@ -74,6 +74,7 @@ struct Coef {
   Real M, I;
   float skin_half2;  // (skin/2)^2
   float rl_ss2, rl_cr2, rl_max2;
+  Real khb_gc;       // hydrogen-bond coefficient of G.C pairs (Sec. 5)
   double dt_d;       // FP64 step for the position accumulation
   double noise_cd;   // FP64 copy of noise_c
 };
@@ -84,6 +85,7 @@ struct KArgs {
   int64_t n;
   int64_t ns;      // row stride of the [component][slot] arrays: n rounded up to a multiple of 32
   int n_mol;
+  int bubble;      // 1: no dihedral / bending inside runs of > 2 open base pairs (Sec. 5)
   int64_t nseg;
   int cap;
   int64_t nsteps;

@@ -54,10 +54,34 @@ __device__ __forceinline__ SegSmem<Real> carve(unsigned char* raw, int /*T*/) {
 // ---------------------------------------------------------------- strip pass
 __device__ __forceinline__ int ring(int64_t g) { return (int)(g & (RING - 1)); }
 
+// Sec. 5: base pair k is open when the hydrogen bond between its patches is
+// broken (distance beyond rc).  mark_open tests the pair whose strand-A slot
+// g = 2k was just staged (with its partner g + 1) and sets F_OPEN on the
+// ring copy of its flags; bp_open reads that bit back.  A pair outside
+// molecule mol (or outside [0, n): flags 0) counts as closed.
+constexpr int F_OPEN = 64;   // ring flags only, never in the topology array
+template <class Real>
+__device__ __forceinline__ void mark_open(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t g) {
+  const int ra = ring(g), rb = ring(g + 1);
+  const int fa = sm.flg[ra];
+  if (fa == 0) return;
+  const SPos<Real> pa = sm.pos[ra], pb = sm.pos[rb];
+  const V3<Real> d = rel(pa, pb) + a.c.h * (uvec(pb) - uvec(pa));
+  if (dot(d, d) > a.c.rchb2) sm.flg[ra] = fa | F_OPEN;
+}
+__device__ __forceinline__ bool bp_open(const int* flg, int64_t k, int mol) {
+  const int fa = flg[ring(2 * k)];
+  return (fa & F_OPEN) && (fa >> 8) == mol;
+}
+
 // Bonded terms owned by slot o (ring index ri): the step o -> next along its
 // strand (FENE + WCA, Morse, dihedral, planarity) and the bending angle at o.
 // Forces go to the owner (cs), its next nucleotide (cn) and the previous
-// patch (cp), so each term is evaluated once.
+// patch (cp), so each term is evaluated once.  With the bubble rule (Sec. 5)
+// the dihedral is left out when both base pairs of the step lie in a run of
+// three or more open pairs, and the bending when the pairs of o and of both
+// its strand neighbours are open; the ring then holds base pairs o/2 - 2 ..
+// o/2 + 2.
 template <class Real>
 __device__ __forceinline__ void owner_terms(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t o, unsigned& fl,
                                             Real* E, Real* W) {
@@ -66,6 +90,16 @@ __device__ __forceinline__ void owner_terms(const KArgs<Real>& a, const SegSmem<
   V3<Real> sb{0, 0, 0}, sp{0, 0, 0}, nb{0, 0, 0}, np{0, 0, 0}, pp{0, 0, 0};
   if (f & F_NEXT) {
     const int dir = (o & 1) ? -2 : 2;   // strand A (even slot) runs up, strand B down
+    bool skip_dih = false, skip_bend = false;
+    if (a.bubble) {
+      const int mol = f >> 8;
+      const int64_t ko = o >> 1, kq = (o + dir) >> 1;
+      if (bp_open(sm.flg, ko, mol) && bp_open(sm.flg, kq, mol)) {
+        const int64_t lo = ko < kq ? ko : kq, hi = ko < kq ? kq : ko;
+        skip_dih = bp_open(sm.flg, lo - 1, mol) || bp_open(sm.flg, hi + 1, mol);
+        skip_bend = (f & F_PREV) && bp_open(sm.flg, (o - dir) >> 1, mol);
+      }
+    }
     const SPos<Real> so = sm.pos[ri];
     const SPos<Real> sq = sm.pos[ring(o + dir)];
     const Real h = a.c.h;
@@ -79,16 +113,18 @@ __device__ __forceinline__ void owner_terms(const KArgs<Real>& a, const SegSmem<
     np += fm; sp -= fm;
     if (W) { vir_add(W, bq - bo, fb); vir_add(W, pq - po, fm); }
     // dihedral A-E-F-B = bead o, patch o, patch q, bead q
-    V3<Real> fA, fE, fF, fB;
-    t_dihedral(a.c, bo, po, pq, bq, fA, fE, fF, fB, E);
-    sb += fA; sp += fE; np += fF; nb += fB;
-    if (W) { vir_add(W, bo, fA); vir_add(W, po, fE); vir_add(W, pq, fF); vir_add(W, bq, fB); }
+    if (!skip_dih) {
+      V3<Real> fA, fE, fF, fB;
+      t_dihedral(a.c, bo, po, pq, bq, fA, fE, fF, fB, E);
+      sb += fA; sp += fE; np += fF; nb += fB;
+      if (W) { vir_add(W, bo, fA); vir_add(W, po, fE); vir_add(W, pq, fF); vir_add(W, bq, fB); }
+    }
     // planarity: vertex patch q between patch o and bead q
     V3<Real> f1, f2;
     t_planar(a.c, po - pq, bq - pq, f1, f2, E);
     sp += f1; nb += f2; np -= (f1 + f2);
     if (W) { vir_add(W, po, f1); vir_add(W, bq, f2); vir_add(W, pq, -(f1 + f2)); }
-    if (f & F_PREV) {
+    if ((f & F_PREV) && !skip_bend) {
       const SPos<Real> sr = sm.pos[ring(o - dir)];
       const V3<Real> pr = rel(so, sr) + h * uvec(sr);
       V3<Real> g1, g2;
@@ -197,14 +233,15 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       const V3<Real> d = rel(me, q) + h * uvec(q) - h * um;   // patch_q - patch_me
       const Real r2 = dot(d, d);
       if (r2 <= a.c.rchb2) {
-        Real k2 = (Real)2 * a.c.khb;
+        const Real khb = (f & F_GC) ? a.c.khb_gc : a.c.khb;   // Sec. 5: A.T / G.C stiffness
+        Real k2 = (Real)2 * khb;
         if (a.c.r0hb != (Real)0) k2 *= (Real)1 - a.c.r0hb * rsqrt_(r2);
         Fp += k2 * d;
         if constexpr (MODE == MODE_ENERGY) {
           if ((g & 1) == 0) {
             const Real r = sqrt_(r2);
             const Real rc = sqrt_(a.c.rchb2);
-            Eb[2] += a.c.khb * ((r - a.c.r0hb) * (r - a.c.r0hb) - (rc - a.c.r0hb) * (rc - a.c.r0hb));
+            Eb[2] += khb * ((r - a.c.r0hb) * (r - a.c.r0hb) - (rc - a.c.r0hb) * (rc - a.c.r0hb));
             vir_add(Wb, d, -(k2 * d));   // force on the partner patch
           }
         }
@@ -364,10 +401,12 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
 }
 
 // One warp's strip: tiles [t0, t1) of SEG slots.  The prologue stages slots
-// s0-4 .. s0+3 and computes owners s0-2 .. s0+1; every tile at base B then
-// stages slots B+4 .. B+35, computes owners B+2 .. B+33 (one per lane) and
-// finishes nucleotides B .. B+31, whose terms come from owners B-2 .. B+33.
-// An owner's energy is counted by the strip that holds its slot.
+// s0-8 .. s0+7 and computes owners s0-2 .. s0+1; every tile at base B then
+// stages slots B+8 .. B+39 (the ring holds B-24 .. B+39), computes owners
+// B+2 .. B+33 (one per lane; with their base-pair neighbourhoods they read
+// slots B-2 .. B+37) and finishes nucleotides B .. B+31, whose terms come
+// from owners B-2 .. B+33.  An owner's energy is counted by the strip that
+// holds its slot.
 template <class Real, int MODE>
 __device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t t0, int64_t t1, int cur,
                            int64_t step, unsigned& fl) {
@@ -375,14 +414,22 @@ __device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_
   const int lane = threadIdx.x & 31;
   const int64_t s0 = t0 * SEG;
   const int64_t s1 = t1 * SEG < a.n ? t1 * SEG : a.n;
-  if (lane < 8) stage_slot(a, sm, cur, s0 - 4 + lane);
+  if (lane < 16) stage_slot(a, sm, cur, s0 - 8 + lane);
   __syncwarp();
+  if (a.bubble) {
+    if (lane < 16 && !(lane & 1)) mark_open(a, sm, s0 - 8 + lane);
+    __syncwarp();
+  }
   if (lane < 4) owner_pass<Real, MODE>(a, sm, s0 - 2 + lane, lane >= 2 && s0 - 2 + lane < s1, fl);
   for (int64_t t = t0; t < t1; ++t) {
     const int64_t B = t * SEG;
     __syncwarp();
-    stage_slot(a, sm, cur, B + 4 + lane);
+    stage_slot(a, sm, cur, B + 8 + lane);
     __syncwarp();
+    if (a.bubble) {
+      if (!(lane & 1)) mark_open(a, sm, B + 8 + lane);
+      __syncwarp();
+    }
     owner_pass<Real, MODE>(a, sm, B + 2 + lane, B + 2 + lane < s1, fl);
     __syncwarp();
     if (B + lane < s1) nucleotide_pass<Real, MODE>(a, sm, B + lane, cur, step, fl);

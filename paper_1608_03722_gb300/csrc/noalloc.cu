@@ -205,6 +205,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   fill_coef_mixed(*p, a.c);
   a.n = n; a.ns = NA_MAX_NT; a.n_mol = n_mol; a.nseg = (n + 31) / 32; a.cap = NA_CAP;
   a.nsteps = 0; a.noise_mode = 0; a.seed_lo = 0; a.seed_hi = 0;
+  a.bubble = p->bubble_rule ? 1 : 0;
   a.spin_budget = 4000000000ull;
   a.X = reinterpret_cast<double*>(b + O_X);
   a.V = nullptr; a.Om = nullptr;

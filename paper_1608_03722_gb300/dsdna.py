@@ -32,13 +32,28 @@ class dsdna_params(C.Structure):
     _fields_ = [(n, C.c_double) for n in _PARAM_DOUBLES] + [
         ("seed", C.c_uint64), ("noise", C.c_int), ("steric_phase", C.c_int), ("box", C.c_double * 3),
         ("skin", C.c_double), ("precision", C.c_int), ("max_neighbors", C.c_int), ("block_threads", C.c_int),
-        ("blocks_per_sm", C.c_int), ("steps_per_graph", C.c_int)]
+        ("blocks_per_sm", C.c_int), ("steps_per_graph", C.c_int), ("bubble_rule", C.c_int), ("K2_gc", C.c_double)]
 
 
 class dsdna_system(C.Structure):
     _fields_ = [("n_mol", C.c_int), ("n_bp", C.POINTER(C.c_int)), ("X", C.POINTER(C.c_double)),
                 ("V", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double)), ("Om", C.POINTER(C.c_double)),
-                ("tether", C.POINTER(C.c_int))]
+                ("tether", C.POINTER(C.c_int)), ("gc", C.POINTER(C.c_byte))]
+
+
+def _system(n_bp, X, V, u, Om, tether, gc):
+    """dsdna_system for the given arrays; returns (struct, arrays to keep alive)."""
+    nb = np.ascontiguousarray(np.atleast_1d(n_bp), dtype=np.int32)
+    n = 2 * int(nb.sum())
+    X, V, u, Om = _f64(X, n), _f64(V, n), _f64(u, n), _f64(Om, n)
+    tt = None if tether is None else np.ascontiguousarray(np.atleast_1d(tether), dtype=np.int32)
+    gg = None if gc is None else np.ascontiguousarray(np.asarray(gc) != 0, dtype=np.int8)
+    if gg is not None and gg.size != n // 2:
+        raise ValueError(f"gc needs one flag per base pair ({n // 2}), got {gg.size}")
+    sys = dsdna_system(len(nb), nb.ctypes.data_as(C.POINTER(C.c_int)), _dp(X), _dp(V), _dp(u), _dp(Om),
+                       None if tt is None else tt.ctypes.data_as(C.POINTER(C.c_int)),
+                       None if gg is None else gg.ctypes.data_as(C.POINTER(C.c_byte)))
+    return sys, (nb, X, V, u, Om, tt, gg)
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -189,15 +204,11 @@ class _TorchAllocator:
 
 
 def dsdna_create(params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, tether=None, stream=None,
-                 allocator="torch"):
-    """Create a context; returns (handle, keepalive).  X/u and V/Om are (n_nt, 3) arrays or None."""
+                 allocator="torch", gc=None):
+    """Create a context; returns (handle, keepalive).  X/u and V/Om are (n_nt, 3) arrays or None;
+    gc is one flag per base pair (1 = G.C, hydrogen-bond stiffness K2_gc) or None."""
     L = load()
-    nb = np.ascontiguousarray(np.atleast_1d(n_bp), dtype=np.int32)
-    n = 2 * int(nb.sum())
-    X, V, u, Om = _f64(X, n), _f64(V, n), _f64(u, n), _f64(Om, n)
-    tt = None if tether is None else np.ascontiguousarray(np.atleast_1d(tether), dtype=np.int32)
-    sys = dsdna_system(len(nb), nb.ctypes.data_as(C.POINTER(C.c_int)), _dp(X), _dp(V), _dp(u), _dp(Om),
-                       None if tt is None else tt.ctypes.data_as(C.POINTER(C.c_int)))
+    sys, _keep = _system(n_bp, X, V, u, Om, tether, gc)
     alloc = None
     if stream is None:
         import torch
@@ -212,15 +223,10 @@ def dsdna_create(params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, te
 
 
 def dsdna_autotune(params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, tether=None, trial_steps=50,
-                   stream=None, allocator="torch"):
+                   stream=None, allocator="torch", gc=None):
     """Fastest (skin, CTA size, CTAs per SM) for this system; returns (params, ns per nucleotide-step)."""
     L = load()
-    nb = np.ascontiguousarray(np.atleast_1d(n_bp), dtype=np.int32)
-    n = 2 * int(nb.sum())
-    X, V, u, Om = _f64(X, n), _f64(V, n), _f64(u, n), _f64(Om, n)
-    tt = None if tether is None else np.ascontiguousarray(np.atleast_1d(tether), dtype=np.int32)
-    sys = dsdna_system(len(nb), nb.ctypes.data_as(C.POINTER(C.c_int)), _dp(X), _dp(V), _dp(u), _dp(Om),
-                       None if tt is None else tt.ctypes.data_as(C.POINTER(C.c_int)))
+    sys, _keep = _system(n_bp, X, V, u, Om, tether, gc)
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
@@ -237,13 +243,13 @@ class Context:
     """One engine context on the current CUDA device and stream."""
 
     def __init__(self, params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, tether=None, stream=None,
-                 allocator="torch"):
+                 allocator="torch", gc=None):
         self.lib = load()
         self.params = params
         self.n_bp = np.ascontiguousarray(np.atleast_1d(n_bp), dtype=np.int32)
         self.n_nt = 2 * int(self.n_bp.sum())
         self.off = np.concatenate([[0], np.cumsum(self.n_bp)]).astype(np.int64)
-        self.h, self._alloc = dsdna_create(params, self.n_bp, X, V, u, Om, tether, stream, allocator)
+        self.h, self._alloc = dsdna_create(params, self.n_bp, X, V, u, Om, tether, stream, allocator, gc)
 
     def _mol_len(self, mol):
         return self.n_nt if mol < 0 else 2 * int(self.n_bp[mol])

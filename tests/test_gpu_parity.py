@@ -323,3 +323,51 @@ def test_c3_full_size_sampled_forces():
     ctx.synchronize()
     assert ctx.info()["rebuilds"] >= 1
     ctx.close()
+
+
+def _open_pairs(X, bps, shift=0.5):
+    """Move the strand-B nucleotide of each listed (global) base pair 0.5 nm
+    radially off its partner: the pair's patches leave the 0.3 nm range."""
+    X = X.copy()
+    for k in bps:
+        r = X[2 * k + 1, :2] - X[2 * k, :2]
+        X[2 * k + 1, :2] += shift * r / np.linalg.norm(r)
+    return X
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_denaturation_rules_match_oracle(prec):
+    """Sec. 5: bubble rule and A.T / G.C hydrogen-bond stiffness.  Two
+    molecules (40 and 23 bp, 126 slots: four tiles and a ragged tail) with
+    open runs of 4 (a bubble), 3 across the first tile boundary (a bubble),
+    2 (not a bubble) and 2 + 2 on either side of the molecule boundary (not a
+    bubble: pairs of another molecule count as closed)."""
+    n_bp = [40, 23]
+    rng = np.random.default_rng(12)
+    X0, u0 = I.straight_helix(40)
+    X1, u1 = I.straight_helix(23, origin=(8.0, 0.0, 0.0))
+    X = np.concatenate([X0, X1]); u = np.concatenate([u0, u1])
+    X, u = I.perturb(X, u, rng, dx=0.02, dtheta=0.05)
+    opened = [5, 6, 7, 8, 15, 16, 17, 26, 27, 38, 39, 40, 41]
+    X = _open_pairs(X, opened)
+    gc = (np.arange(63) % 3 == 1).astype(np.int8)
+    zero = np.zeros_like(X)
+    kw = dict(R0=3.0, K2_gc=9.0)
+    ctx = D.Context(D.dsdna_default_params(precision=prec, bubble_rule=1, **kw), n_bp, X=X, V=zero, u=u, Om=zero,
+                    gc=gc)
+    Fb, Fp = ctx.compute_forces()
+    E, _ = ctx.energy_virial()
+    Xs, _, us, _ = ctx.get_state()
+    ctx.close()
+    po = O.params(bubble_rule=1, gc=gc, **kw)
+    r = O.forces(po, n_bp, Xs, us)
+    Sb, Sp = O.force_scale(po, n_bp, Xs, us)
+    eb, ep = excess(Fb, r["Fb"], Sb, prec), excess(Fp, r["Fp"], Sp, prec)
+    assert eb < 1.0 and ep < 1.0, (eb, ep)
+    Eo = r["energy"].sum(axis=0)[:8]
+    tol = 1e-9 if prec == D.PREC_FP64 else 2e-5
+    assert np.abs(E[:8] - Eo).max() < tol * np.abs(Eo).sum(), (E[:8], Eo)
+    # the rule and the sequence change this configuration's energy
+    Eoff = O.forces(O.params(**kw), n_bp, Xs, us)["energy"].sum(axis=0)
+    assert Eoff[D.E_DIHEDRAL] - Eo[D.E_DIHEDRAL] > 1e-3 or Eo[D.E_DIHEDRAL] - Eoff[D.E_DIHEDRAL] > 1e-3
+    assert abs(Eoff[D.E_HBOND] - Eo[D.E_HBOND]) > 1e-3
