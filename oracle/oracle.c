@@ -21,6 +21,14 @@
  *   or_observables    ideal-helix twist (36 deg / bp), rise, denatured
  *                     fraction limits; Lk of a Hopf link and of torus links
  *                     against a crossing count
+ *   rings (ring[m])   planar ring wound lk times: Lk = Tw = lk, Wr = 0,
+ *                     bending energy 2N K6 (1 - cos(2 pi/N)); energy and twist
+ *                     equal to sums over the N linear cuts (each step term
+ *                     missing once, each bend and twist increment twice);
+ *                     invariance under cyclic relabelling; finite differences
+ *                     across the junction; Lk conserved by dynamics
+ *   Sec. 5 rules      closed-form H-bond depths per pair type, bubble energy
+ *                     removal, finite differences with the rule on
  * Parity unpinned: absolute dynamical time scales (masses, friction) which
  * the paper does not measure.
  */
@@ -55,7 +63,7 @@ void or_default_params(or_params* p) {
   /* App. A: kT = 1, gamma = 1 in simulation units, dt = 0.005 tau_Br (Eq. 16) */
   p->kT = 1.0; p->gamma = 1.0; p->dt = 0.005;
   p->seed = 0; p->noise = 1; p->steric_phase = 0;
-  p->bubble_rule = 0; p->K2_gc = 0.0; p->gc = NULL;
+  p->bubble_rule = 0; p->K2_gc = 0.0; p->gc = NULL; p->ring = NULL;
   p->box[0] = p->box[1] = p->box[2] = 0.0;
 }
 
@@ -85,16 +93,21 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 typedef struct {
   int n_mol;
   const int* n_bp;
+  const signed char* ring;   /* per molecule, 1 = circular (may be NULL) */
   int64_t* off;     /* bp offset of each molecule */
   int64_t n_nt;
 } topo_t;
 
-static int topo_init(topo_t* t, int n_mol, const int* n_bp) {
-  t->n_mol = n_mol; t->n_bp = n_bp;
+static int topo_init(topo_t* t, const or_params* p, int n_mol, const int* n_bp) {
+  t->n_mol = n_mol; t->n_bp = n_bp; t->ring = p->ring;
   t->off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_mol + 1));
   if (!t->off) return OR_EINVAL;
   int64_t o = 0;
-  for (int m = 0; m < n_mol; ++m) { t->off[m] = o; if (n_bp[m] < 1) { free(t->off); return OR_EINVAL; } o += n_bp[m]; }
+  for (int m = 0; m < n_mol; ++m) {
+    t->off[m] = o;
+    if (n_bp[m] < 1 || (t->ring && t->ring[m] && n_bp[m] < 6)) { free(t->off); return OR_EINVAL; }
+    o += n_bp[m];
+  }
   t->off[n_mol] = o;
   t->n_nt = 2 * o;
   return OR_OK;
@@ -107,16 +120,25 @@ static int mol_of(const topo_t* t, int64_t g) {
   while (lo < hi) { int mid = (lo + hi + 1) / 2; if (t->off[mid] <= bp) lo = mid; else hi = mid - 1; }
   return lo;
 }
-/* next / previous nucleotide along the same strand in 5'->3' order (Sec. 2) */
+static int is_ring(const topo_t* t, int m) { return t->ring && t->ring[m]; }
+/* nucleotide on strand (g & 1) of base pair k of molecule m, k taken modulo
+ * N on a ring; -1 past the end of a linear molecule */
+static int64_t nt_at(const topo_t* t, int m, int64_t k, int64_t g) {
+  const int N = t->n_bp[m];
+  if (is_ring(t, m)) k = ((k % N) + N) % N;
+  else if (k < 0 || k >= N) return -1;
+  return 2 * (t->off[m] + k) + (g & 1);
+}
+/* next / previous nucleotide along the same strand in 5'->3' order (Sec. 2):
+ * strand A (even slots) runs to increasing k, strand B to decreasing k; on a
+ * ring the last nucleotide of a strand is followed by its first. */
 static int64_t next_nt(const topo_t* t, int64_t g) {
-  int m = mol_of(t, g); int64_t k = g / 2 - t->off[m]; int N = t->n_bp[m];
-  if ((g & 1) == 0) return (k + 1 < N) ? g + 2 : -1;
-  return (k - 1 >= 0) ? g - 2 : -1;
+  int m = mol_of(t, g); int64_t k = g / 2 - t->off[m];
+  return nt_at(t, m, (g & 1) == 0 ? k + 1 : k - 1, g);
 }
 static int64_t prev_nt(const topo_t* t, int64_t g) {
-  int m = mol_of(t, g); int64_t k = g / 2 - t->off[m]; int N = t->n_bp[m];
-  if ((g & 1) == 0) return (k - 1 >= 0) ? g - 2 : -1;
-  return (k + 1 < N) ? g + 2 : -1;
+  int m = mol_of(t, g); int64_t k = g / 2 - t->off[m];
+  return nt_at(t, m, (g & 1) == 0 ? k - 1 : k + 1, g);
 }
 /* Sec. 2 / Fig. 1d: along each strand one sterically interacting bead is
  * followed by two ghost beads; the index is counted 5'->3'. */
@@ -301,9 +323,11 @@ static void tout_add(tout_t* o, int64_t slot, int site, const double* f, const d
 
 /* Sec. 5: a base pair is open (denatured) when its hydrogen bond is broken,
  * r^2 > rc^2 between the paired patches; a base pair outside molecule m
- * counts as closed. */
+ * counts as closed (on a ring the index is taken modulo its length). */
 static int bp_open(const or_params* p, const topo_t* t, const double* X, const double* u, int m, int64_t bp) {
-  if (bp < t->off[m] || bp >= t->off[m] + t->n_bp[m]) return 0;
+  const int64_t g = nt_at(t, m, bp - t->off[m], 0);
+  if (g < 0) return 0;
+  bp = g / 2;
   double pa[3], pb[3], d[3];
   site_pos(p, X, u, 2 * bp, 1, pa);
   site_pos(p, X, u, 2 * bp + 1, 1, pb);
@@ -351,9 +375,11 @@ static int owner_terms(const or_params* p, const topo_t* t, const double* X, con
     double rE[3], rF[3], rB[3], fA[3], fE[3], fF[3], fB[3];
     int in_bubble = 0;
     if (p->bubble_rule) {
-      const int64_t kg = g / 2, kn = n / 2, lo = kg < kn ? kg : kn, hi = kg < kn ? kn : kg;
-      in_bubble = bp_open(p, t, X, u, m, kg) && bp_open(p, t, X, u, m, kn) &&
-                  (bp_open(p, t, X, u, m, lo - 1) || bp_open(p, t, X, u, m, hi + 1));
+      /* pairs kg -> kg + s of the step (s = +1 strand A, -1 strand B) and
+       * the pairs that flank it, kg - s and kg + 2s */
+      const int64_t kg = g / 2, s = (g & 1) == 0 ? 1 : -1;
+      in_bubble = bp_open(p, t, X, u, m, kg) && bp_open(p, t, X, u, m, kg + s) &&
+                  (bp_open(p, t, X, u, m, kg - s) || bp_open(p, t, X, u, m, kg + 2 * s));
     }
     if (!in_bubble) {
       disp(p, bg, pg, rE); disp(p, bg, pn, rF); disp(p, bg, bn, rB);
@@ -562,7 +588,7 @@ static int forces_impl(const or_params* p, int n_mol, const int* n_bp, const dou
                        const double* ef, const double* et, double* Fb, double* Fp, double* Fbody, double* Tbody,
                        double* energy, double* virial, int use_cells, double* Sb, double* Sp) {
   topo_t t;
-  if (topo_init(&t, n_mol, n_bp) != OR_OK) return OR_EINVAL;
+  if (topo_init(&t, p, n_mol, n_bp) != OR_OK) return OR_EINVAL;
   int64_t n = t.n_nt;
   double* fb = Fb ? Fb : (double*)calloc((size_t)(3 * n), sizeof(double));
   double* fp = Fp ? Fp : (double*)calloc((size_t)(3 * n), sizeof(double));
@@ -620,7 +646,7 @@ int or_forces_sampled(const or_params* p, int n_mol, const int* n_bp, const doub
                       const double* ef, const double* et, int ns, const int64_t* idx, double* Fb, double* Fp,
                       double* Sb, double* Sp) {
   topo_t t;
-  if (topo_init(&t, n_mol, n_bp) != OR_OK) return OR_EINVAL;
+  if (topo_init(&t, p, n_mol, n_bp) != OR_OK) return OR_EINVAL;
   int rc = OR_OK;
   for (int q = 0; q < ns && rc == OR_OK; ++q) {
     int64_t g = idx[q];
@@ -680,7 +706,7 @@ int or_forces_sampled(const or_params* p, int n_mol, const int* n_bp, const doub
 int64_t or_pairs(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
                  double extra, int64_t cap, int64_t* pi, int64_t* pj) {
   topo_t t;
-  if (topo_init(&t, n_mol, n_bp) != OR_OK) return -1;
+  if (topo_init(&t, p, n_mol, n_bp) != OR_OK) return -1;
   int64_t cnt = 0;
   for (int m = 0; m < n_mol; ++m) {
     int64_t g0 = 2 * t.off[m], g1 = 2 * t.off[m + 1];
@@ -825,7 +851,7 @@ static void total_force(const or_params* p, int mol, int64_t local, int64_t step
 int or_run(const or_params* p, int n_mol, const int* n_bp, double* X, double* V, double* u, double* Om,
            const double* ef, const double* et, const int* tether, int64_t step0, int64_t nsteps, int use_cells) {
   topo_t t;
-  if (topo_init(&t, n_mol, n_bp) != OR_OK) return OR_EINVAL;
+  if (topo_init(&t, p, n_mol, n_bp) != OR_OK) return OR_EINVAL;
   int64_t n = t.n_nt;
   double* F = (double*)malloc(sizeof(double) * (size_t)(3 * n));
   double* T = (double*)malloc(sizeof(double) * (size_t)(3 * n));
@@ -871,7 +897,7 @@ int or_energy(const or_params* p, int n_mol, const int* n_bp, const double* X, c
               const double* u, const double* Om, const double* ef, const double* et,
               const int* tether, int64_t step, double* energy, double* virial) {
   topo_t t;
-  if (topo_init(&t, n_mol, n_bp) != OR_OK) return OR_EINVAL;
+  if (topo_init(&t, p, n_mol, n_bp) != OR_OK) return OR_EINVAL;
   int64_t n = t.n_nt;
   double* F = (double*)malloc(sizeof(double) * (size_t)(3 * n));
   double* T = (double*)malloc(sizeof(double) * (size_t)(3 * n));
@@ -959,7 +985,7 @@ static void close_curve(const double* c, int N, const double* e, const double* e
 int or_observables(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
                    int mol, int with_lk, double* out) {
   topo_t t;
-  if (topo_init(&t, n_mol, n_bp) != OR_OK || mol < 0 || mol >= n_mol) return OR_EINVAL;
+  if (topo_init(&t, p, n_mol, n_bp) != OR_OK || mol < 0 || mol >= n_mol) return OR_EINVAL;
   int N = n_bp[mol];
   int64_t g0 = 2 * t.off[mol];
   double* mid = (double*)malloc(sizeof(double) * 3 * (size_t)N);
@@ -983,13 +1009,17 @@ int or_observables(const or_params* p, int n_mol, const int* n_bp, const double*
   out[0] = mid[3 * (N - 1) + 2] - mid[2];
   out[1] = (double)denat / (double)N;
   /* Sec. 3.2 / App. B: frames (f, v, t) per base-pair step; twist increment
-   * alpha + gamma of the ZYZ Euler rotation between consecutive frames. */
+   * alpha + gamma of the ZYZ Euler rotation between consecutive frames.  A
+   * ring has N steps (the last one closes it) and N increments, a linear
+   * molecule N - 1 steps and N - 2 increments. */
+  const int ring = is_ring(&t, mol);
+  const int nfr = ring ? N : N - 1, ninc = ring ? N : N - 2;
   double tw = 0.0;
   if (N >= 3) {
-    double (*fr)[3][3] = malloc(sizeof(double[3][3]) * (size_t)(N - 1));
-    for (int k = 0; k < N - 1; ++k) {
+    double (*fr)[3][3] = malloc(sizeof(double[3][3]) * (size_t)nfr);
+    for (int k = 0; k < nfr; ++k) {
       double tv[3], w[3];
-      v_sub(mid + 3 * (k + 1), mid + 3 * k, tv);
+      v_sub(mid + 3 * ((k + 1) % N), mid + 3 * k, tv);
       double l = v_norm(tv);
       for (int c = 0; c < 3; ++c) tv[c] /= l;
       v_sub(bB + 3 * k, bA + 3 * k, w);
@@ -1001,18 +1031,22 @@ int or_observables(const or_params* p, int n_mol, const int* n_bp, const double*
       v_cross(tv, w, vv);
       for (int c = 0; c < 3; ++c) { fr[k][0][c] = w[c]; fr[k][1][c] = vv[c]; fr[k][2][c] = tv[c]; }
     }
-    for (int k = 0; k < N - 2; ++k) {
+    for (int k = 0; k < ninc; ++k) {
       double R[3][3];
-      for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) R[i][j] = v_dot(fr[k][i], fr[k + 1][j]);
+      for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) R[i][j] = v_dot(fr[k][i], fr[(k + 1) % nfr][j]);
       tw += atan2(R[1][0] - R[0][1], R[0][0] + R[1][1]);
     }
     free(fr);
     tw /= 2.0 * PI;
   }
   out[2] = tw;
-  out[3] = (N >= 3) ? (double)(N - 2) * (p->d_dih + PI) / (2.0 * PI) : 0.0;
+  out[3] = (N >= 3) ? (double)ninc * (p->d_dih + PI) / (2.0 * PI) : 0.0;
   out[4] = out[5] = 0.0;
-  if (with_lk && N >= 2) {
+  if (with_lk && ring) {
+    /* App. C Eq. 17 on the two closed bead curves of a ring: no closure */
+    out[4] = or_linking_number(N, bA, N, bB);
+    out[5] = out[4] - out[2];
+  } else if (with_lk && N >= 2) {
     double e[3];
     v_sub(mid + 3 * (N - 1), mid, e);
     double le = v_norm(e);

@@ -69,6 +69,9 @@ typedef struct {
   int bubble_rule;                     /* 1: no dihedral / bending inside bubbles of > 2 open base pairs */
   double K2_gc;                        /* hydrogen-bond stiffness of G.C pairs (<= 0: K2) */
   const signed char* gc;               /* per base pair over all molecules: 1 = G.C, 0 = A.T (NULL: all K2) */
+  /* Sec. 6 supercoiled rings: per molecule, 1 = circular (each strand's last
+   * nucleotide bonded to its first; at least 6 bp), 0 = linear (NULL: all linear) */
+  const signed char* ring;
 } or_params;
 
 void or_default_params(or_params* p);

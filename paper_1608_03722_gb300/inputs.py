@@ -75,6 +75,23 @@ def straight_helix(n_bp: int, origin=(0.0, 0.0, 0.0)):
     return place(axis, d)
 
 
+def ring_helix(n_bp: int, lk: int, center=(0.0, 0.0, 0.0)):
+    """Planar circular duplex of n_bp base pairs in the xy plane whose bead
+    direction turns lk times about the local tangent (linking number lk of
+    the two closed strands; lk = n_bp/10 is torsionally relaxed).  The axis
+    points sit on a regular n_bp-gon with sides of one rise."""
+    k = np.arange(n_bp)
+    R = RISE / (2.0 * math.sin(math.pi / n_bp))
+    th = 2.0 * math.pi * k / n_bp
+    nrm = np.stack([np.cos(th), np.sin(th), np.zeros(n_bp)], axis=1)     # radial
+    tan = np.stack([-np.sin(th), np.cos(th), np.zeros(n_bp)], axis=1)    # tangent, strand A direction
+    b = np.cross(tan, nrm)
+    axis = np.asarray(center, float)[None, :] + R * nrm
+    ang = 2.0 * math.pi * lk * k / n_bp
+    d = np.cos(ang)[:, None] * nrm + np.sin(ang)[:, None] * b
+    return place(axis, d)
+
+
 def maxwell(u: np.ndarray, rng: np.random.Generator, kT: float = 1.0, mass: float = 1.0, ell: float = ELL,
             frozen: np.ndarray | None = None):
     """Maxwell-Boltzmann centre and angular velocities (angular normal to u)."""
