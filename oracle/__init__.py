@@ -27,7 +27,8 @@ class Params(C.Structure):
         "K1", "R0", "eps_bb", "sigma_bb", "K2", "r0_hb", "rc_hb", "eps_ev", "sigma_ss", "sigma_cross",
         "K3", "d_dih", "K4", "lambda_m", "r0_m", "K5", "alpha0", "K6", "mass", "ell", "kT", "gamma", "dt")] + [
         ("seed", C.c_uint64), ("noise", C.c_int), ("steric_phase", C.c_int), ("box", C.c_double * 3),
-        ("bubble_rule", C.c_int), ("K2_gc", C.c_double), ("gc", C.c_void_p), ("ring", C.c_void_p)]
+        ("bubble_rule", C.c_int), ("K2_gc", C.c_double), ("gc", C.c_void_p), ("ring", C.c_void_p),
+        ("removed", C.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -88,6 +89,11 @@ def params(**kw) -> Params:
         if k == "box":
             for c in range(3):
                 p.box[c] = float(v[c])
+        elif k == "removed":   # bubble rule 2 mask, uint8 per nucleotide, shared (or_run updates it in place)
+            if v is not None:
+                assert v.dtype == np.uint8 and v.flags.c_contiguous
+            p._removed_keep = v
+            p.removed = None if v is None else v.ctypes.data
         elif k in ("gc", "ring"):   # G.C flag per base pair / circular flag per molecule (kept alive with p)
             arr = None if v is None else np.ascontiguousarray(np.atleast_1d(v), dtype=np.int8)
             setattr(p, "_" + k + "_keep", arr)

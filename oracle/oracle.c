@@ -63,7 +63,7 @@ void or_default_params(or_params* p) {
   /* App. A: kT = 1, gamma = 1 in simulation units, dt = 0.005 tau_Br (Eq. 16) */
   p->kT = 1.0; p->gamma = 1.0; p->dt = 0.005;
   p->seed = 0; p->noise = 1; p->steric_phase = 0;
-  p->bubble_rule = 0; p->K2_gc = 0.0; p->gc = NULL; p->ring = NULL;
+  p->bubble_rule = 0; p->K2_gc = 0.0; p->gc = NULL; p->ring = NULL; p->removed = NULL;
   p->box[0] = p->box[1] = p->box[2] = 0.0;
 }
 
@@ -345,8 +345,13 @@ static double pair_K2(const or_params* p, int64_t bp) {
  * its strand in 5'->3' order, plus the bending term centred on g).  With the
  * bubble rule of Sec. 5 the dihedral of the step g -> n is left out when both
  * base pairs lie in a run of at least three consecutive open base pairs, and
- * the bending at g when its three base pairs are all open. */
-static int owner_terms(const or_params* p, const topo_t* t, const double* X, const double* u, int64_t g, tout_t* o) {
+ * the bending at g when its three base pairs are all open.  Rule 2 also
+ * leaves out what the mask p->removed marks, and records in upd[g] (when not
+ * NULL) what this evaluation left out. */
+static int owner_terms(const or_params* p, const topo_t* t, const double* X, const double* u, int64_t g, tout_t* o,
+                       unsigned char* upd) {
+  const unsigned rm0 = (p->bubble_rule == 2 && p->removed) ? p->removed[g] : 0u;
+  unsigned rm1 = rm0;
   static const double zero[3] = {0, 0, 0};
   int64_t n = next_nt(t, g), pv = prev_nt(t, g);
   const int m = mol_of(t, g);
@@ -381,7 +386,8 @@ static int owner_terms(const or_params* p, const topo_t* t, const double* X, con
       in_bubble = bp_open(p, t, X, u, m, kg) && bp_open(p, t, X, u, m, kg + s) &&
                   (bp_open(p, t, X, u, m, kg - s) || bp_open(p, t, X, u, m, kg + 2 * s));
     }
-    if (!in_bubble) {
+    if (in_bubble) rm1 |= 1u;
+    if (!(rm1 & 1u)) {
       disp(p, bg, pg, rE); disp(p, bg, pn, rF); disp(p, bg, bn, rB);
       term_dihedral(p, rE, rF, rB, &e1, fA, fE, fF, fB, NULL);
       o->e[OR_E_DIHEDRAL] += e1;
@@ -395,8 +401,11 @@ static int owner_terms(const or_params* p, const topo_t* t, const double* X, con
     disp(p, pg, pn, rpn); disp(p, pg, bn, rbn);
     tout_add(o, g, 1, fE, zero); tout_add(o, n, 1, fF, rpn); tout_add(o, n, 0, fB, rbn);
   }
-  if (n >= 0 && pv >= 0 &&
-      !(p->bubble_rule && bp_open(p, t, X, u, m, pv / 2) && bp_open(p, t, X, u, m, g / 2) && bp_open(p, t, X, u, m, n / 2))) {
+  if (n >= 0 && pv >= 0 && p->bubble_rule && bp_open(p, t, X, u, m, pv / 2) && bp_open(p, t, X, u, m, g / 2) &&
+      bp_open(p, t, X, u, m, n / 2))
+    rm1 |= 2u;
+  if (upd && p->bubble_rule == 2) upd[g] = (unsigned char)rm1;
+  if (n >= 0 && pv >= 0 && !(rm1 & 2u)) {
     double pp[3], pn[3], v1[3], v2[3], f1[3], fv[3], f2[3], e1, r1[3], r2[3];
     site_pos(p, X, u, pv, 1, pp);
     site_pos(p, X, u, n, 1, pn);
@@ -586,7 +595,7 @@ static void all_pairs(const or_params* p, const topo_t* t, const double* X, cons
 
 static int forces_impl(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
                        const double* ef, const double* et, double* Fb, double* Fp, double* Fbody, double* Tbody,
-                       double* energy, double* virial, int use_cells, double* Sb, double* Sp) {
+                       double* energy, double* virial, int use_cells, double* Sb, double* Sp, unsigned char* upd) {
   topo_t t;
   if (topo_init(&t, p, n_mol, n_bp) != OR_OK) return OR_EINVAL;
   int64_t n = t.n_nt;
@@ -603,7 +612,7 @@ static int forces_impl(const or_params* p, int n_mol, const int* n_bp, const dou
   for (int64_t g = 0; g < n && rc == OR_OK; ++g) {
     tout_t o; memset(&o, 0, sizeof(o));
     int m = mol_of(&t, g);
-    if (owner_terms(p, &t, X, u, g, &o) != OR_OK) { rc = OR_EFENE; break; }
+    if (owner_terms(p, &t, X, u, g, &o, upd) != OR_OK) { rc = OR_EFENE; break; }
     if ((g & 1) == 0) hbond_terms(p, X, u, g, &o);
     sink_tout(&s, &o, m);
   }
@@ -630,16 +639,16 @@ static int forces_impl(const or_params* p, int n_mol, const int* n_bp, const dou
 int or_forces(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
               const double* ef, const double* et, double* Fb, double* Fp, double* Fbody, double* Tbody,
               double* energy, double* virial) {
-  return forces_impl(p, n_mol, n_bp, X, u, ef, et, Fb, Fp, Fbody, Tbody, energy, virial, 0, NULL, NULL);
+  return forces_impl(p, n_mol, n_bp, X, u, ef, et, Fb, Fp, Fbody, Tbody, energy, virial, 0, NULL, NULL, NULL);
 }
 int or_force_scale(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
                    const double* ef, const double* et, double* Sb, double* Sp) {
-  return forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, NULL, NULL, NULL, NULL, 1, Sb, Sp);
+  return forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, NULL, NULL, NULL, NULL, 1, Sb, Sp, NULL);
 }
 int or_forces_cells(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
                     const double* ef, const double* et, double* Fb, double* Fp, double* Fbody, double* Tbody,
                     double* energy, double* virial) {
-  return forces_impl(p, n_mol, n_bp, X, u, ef, et, Fb, Fp, Fbody, Tbody, energy, virial, 1, NULL, NULL);
+  return forces_impl(p, n_mol, n_bp, X, u, ef, et, Fb, Fp, Fbody, Tbody, energy, virial, 1, NULL, NULL, NULL);
 }
 
 int or_forces_sampled(const or_params* p, int n_mol, const int* n_bp, const double* X, const double* u,
@@ -656,7 +665,7 @@ int or_forces_sampled(const or_params* p, int n_mol, const int* n_bp, const doub
     for (int k = 0; k < 3; ++k) {
       if (owners[k] < 0) continue;
       tout_t o; memset(&o, 0, sizeof(o));
-      if (owner_terms(p, &t, X, u, owners[k], &o) != OR_OK) { rc = OR_EFENE; break; }
+      if (owner_terms(p, &t, X, u, owners[k], &o, NULL) != OR_OK) { rc = OR_EFENE; break; }
       for (int i = 0; i < o.n; ++i) if (o.c[i].slot == g) {
         double* F = o.c[i].site == 0 ? fb : fp;
         for (int c = 0; c < 3; ++c) F[c] += o.c[i].f[c];
@@ -856,9 +865,15 @@ int or_run(const or_params* p, int n_mol, const int* n_bp, double* X, double* V,
   double* F = (double*)malloc(sizeof(double) * (size_t)(3 * n));
   double* T = (double*)malloc(sizeof(double) * (size_t)(3 * n));
   double M = 2.0 * p->mass, I = 0.5 * p->mass * p->ell * p->ell;
+  /* rule 2: the mask carries across steps; each force evaluation reads it and
+   * adds what it left out */
+  or_params q = *p;
+  unsigned char* own = NULL;
+  if (q.bubble_rule == 2 && !q.removed) q.removed = own = (unsigned char*)calloc((size_t)n, 1);
   int rc = OR_OK;
   for (int64_t s = step0; s < step0 + nsteps; ++s) {
-    rc = forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, F, T, NULL, NULL, use_cells, NULL, NULL);
+    rc = forces_impl(&q, n_mol, n_bp, X, u, ef, et, NULL, NULL, F, T, NULL, NULL, use_cells, NULL, NULL,
+                     q.bubble_rule == 2 ? q.removed : NULL);
     if (rc != OR_OK) break;
     for (int64_t g = 0; g < n; ++g) {
       int m = mol_of(&t, g);
@@ -888,7 +903,7 @@ int or_run(const or_params* p, int n_mol, const int* n_bp, double* X, double* V,
       }
     }
   }
-  free(F); free(T);
+  free(F); free(T); free(own);
   topo_free(&t);
   return rc;
 }
@@ -901,7 +916,7 @@ int or_energy(const or_params* p, int n_mol, const int* n_bp, const double* X, c
   int64_t n = t.n_nt;
   double* F = (double*)malloc(sizeof(double) * (size_t)(3 * n));
   double* T = (double*)malloc(sizeof(double) * (size_t)(3 * n));
-  int rc = forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, F, T, energy, virial, 0, NULL, NULL);
+  int rc = forces_impl(p, n_mol, n_bp, X, u, ef, et, NULL, NULL, F, T, energy, virial, 0, NULL, NULL, NULL);
   double M = 2.0 * p->mass, I = 0.5 * p->mass * p->ell * p->ell;
   if (rc == OR_OK && energy) {
     for (int64_t g = 0; g < n; ++g) {

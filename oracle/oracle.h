@@ -66,12 +66,18 @@ typedef struct {
   int steric_phase;                    /* steric iff (index along strand) % 3 == phase */
   double box[3];                       /* > 0: periodic edge; <= 0: open */
   /* Sec. 5 denaturation */
-  int bubble_rule;                     /* 1: no dihedral / bending inside bubbles of > 2 open base pairs */
+  int bubble_rule;                     /* no dihedral / bending inside bubbles of > 2 open base pairs:
+                                          0 off, 1 while the bubble lasts, 2 for good once inside one */
   double K2_gc;                        /* hydrogen-bond stiffness of G.C pairs (<= 0: K2) */
   const signed char* gc;               /* per base pair over all molecules: 1 = G.C, 0 = A.T (NULL: all K2) */
   /* Sec. 6 supercoiled rings: per molecule, 1 = circular (each strand's last
    * nucleotide bonded to its first; at least 6 bp), 0 = linear (NULL: all linear) */
   const signed char* ring;
+  /* bubble_rule 2: per nucleotide slot, bit 0 = dihedral of the step to the
+   * next nucleotide removed, bit 1 = bending centred on it removed.  Read by
+   * every force evaluation, extended by or_run (NULL: nothing removed yet; or_run
+   * then keeps its own mask for the run). */
+  unsigned char* removed;
 } or_params;
 
 void or_default_params(or_params* p);

@@ -104,3 +104,76 @@ def test_forces_with_bubble_and_sequence_are_minus_energy_gradient():
                 fd = -(vals[0] - vals[1]) / (2 * h)
                 an = (r["Fb"] if site == 0 else r["Fp"])[g, c]
                 assert abs(an - fd) < 1e-6 * max(1.0, abs(fd)), (g, site, c, an, fd)
+
+
+def _inner_mask(N, a, b):
+    """Removed-term mask of a bubble over base pairs a..b (bits: 1 dihedral of
+    the step to the next nucleotide, 2 bending centred on the nucleotide)."""
+    m = np.zeros(2 * N, np.uint8)
+    for k in range(a, b):
+        m[2 * k] |= 1            # strand A step k -> k + 1
+        m[2 * (k + 1) + 1] |= 1  # strand B step k + 1 -> k
+    for k in range(a + 1, b):
+        m[2 * k] |= 2
+        m[2 * k + 1] |= 2
+    return m
+
+
+@pytest.mark.parametrize("bubble", [(4, 5, 6), (0, 1, 2, 3), (8, 9, 10, 11)])
+def test_permanent_rule_equals_while_rule_without_history(bubble):
+    """Rule 2 with an empty mask evaluates exactly what rule 1 does."""
+    N = 12
+    X, u = _perturbed(N, 3)
+    X = _open(X, bubble)
+    r1 = O.forces(O.params(R0=3.0, bubble_rule=1), N, X, u)
+    r2 = O.forces(O.params(R0=3.0, bubble_rule=2), N, X, u)
+    for k in ("Fb", "Fp", "energy"):
+        assert np.array_equal(r1[k], r2[k])
+
+
+def test_mask_removes_exactly_the_marked_terms_of_a_closed_molecule():
+    """A closed duplex with the mask of a former bubble over pairs 3..6: its
+    energy lacks the dihedral and bending energy of a molecule made of those
+    pairs alone; the forces are minus the gradient of that energy."""
+    N = 12
+    X, u = _perturbed(N, 8)
+    mask = _inner_mask(N, 3, 6)
+    p = O.params(bubble_rule=2, removed=mask)
+    on, off = _E(p, N, X, u), _E(O.params(), N, X, u)
+    inner = _E(O.params(), 4, X[6:14], u[6:14])
+    assert abs((off[4] - on[4]) - inner[4]) < 1e-12 and inner[4] > 0.0
+    assert abs((off[7] - on[7]) - inner[7]) < 1e-12
+    assert _E(O.params(bubble_rule=1, removed=mask), N, X, u)[4] == off[4]   # rule 1 ignores the mask
+    r = O.forces(p, N, X, u)
+    b, pt = O.sites(p, X, u)
+    h = 1e-6
+    for g in (6, 9, 13):
+        for c in range(3):
+            vals = []
+            for sgn in (1, -1):
+                pp = pt.copy()
+                pp[g, c] += sgn * h
+                vals.append(_E(p, N, 0.5 * (b + pp), (pp - b) / p.ell)[:8].sum())
+            assert abs(r["Fp"][g, c] + (vals[0] - vals[1]) / (2 * h)) < 1e-6 * max(1.0, abs(r["Fp"][g, c]))
+
+
+def test_run_records_bubbles_and_keeps_them_removed():
+    """One step from a configuration with a bubble over pairs 3..6 records
+    exactly that bubble's inner terms; after the bubble closes again (the
+    original duplex) another step keeps them removed."""
+    N = 12
+    X0, u0 = _perturbed(N, 9)
+    X = _open(X0, [3, 4, 5, 6])
+    mask = np.zeros(2 * N, np.uint8)
+    p = O.params(R0=3.0, bubble_rule=2, removed=mask, noise=0, dt=1e-6)
+    V = np.zeros_like(X); Om = np.zeros_like(X)
+    Xr, ur = X.copy(), u0.copy()
+    O.run(p, N, Xr, V.copy(), ur, Om.copy(), 1)
+    assert np.array_equal(mask, _inner_mask(N, 3, 6))
+    Xc, uc = X0.copy(), u0.copy()
+    O.run(p, N, Xc, V.copy(), uc, Om.copy(), 1)
+    assert np.array_equal(mask, _inner_mask(N, 3, 6))
+    free = np.zeros(2 * N, np.uint8)
+    O.run(O.params(R0=3.0, bubble_rule=2, removed=free, noise=0, dt=1e-6), N, X0.copy(), V.copy(), u0.copy(),
+          Om.copy(), 1)
+    assert not free.any()
