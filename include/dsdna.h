@@ -118,20 +118,29 @@ typedef struct dsdna_params {
   int blocks_per_sm;                     /* persistent CTAs per SM (0: as many as fit) */
   int steps_per_graph;                   /* steps per captured CUDA graph launch (0: default 50) */
   /* Sec. 5 denaturation.  A base pair is open when its hydrogen bond is
-   * broken (patch distance > rc_hb).  With bubble_rule = 1 the dihedral of a
+   * broken (patch distance > rc_hb).  With the bubble rule the dihedral of a
    * strand step is left out when both of its base pairs lie in a run of at
    * least three consecutive open base pairs, and the bending angle at a
    * nucleotide when the base pairs of it and of its two strand neighbours are
-   * all open.  K2_gc is the hydrogen-bond stiffness of base pairs flagged G.C
-   * in dsdna_system.gc (<= 0: K2 for every pair). */
-  int bubble_rule;                       /* 0 or 1 */
+   * all open.  bubble_rule = 1: only while that holds (the terms return when
+   * the bubble closes; a returning dihedral can carry tens of kT, which makes
+   * runs at low K2 unstable); 2: for good, recorded in a per-nucleotide mask
+   * (dsdna_get_bubble_mask) that each step extends.  K2_gc is the
+   * hydrogen-bond stiffness of base pairs flagged G.C in dsdna_system.gc
+   * (<= 0: K2 for every pair). */
+  int bubble_rule;                       /* 0 off, 1 while in a bubble, 2 for good */
   double K2_gc;
 } dsdna_params;
 
 /* Molecules and (optional) initial state.  NULL X/u builds ideal relaxed
  * helices along +z from the origin (Sec. 2); NULL V/Om draws Maxwell-Boltzmann
  * velocities from the Philox stream of the seed.  tether[m] != 0 anchors base
- * pair 0 of molecule m (Sec. 4.1).  Molecules never interact with each other. */
+ * pair 0 of molecule m (Sec. 4.1).  circular[m] != 0 closes molecule m into a
+ * ring (the supercoiled rings of Sec. 6 / Fig. 10): on each strand the last
+ * nucleotide is bonded to the first with every bonded term of a strand step,
+ * so the linking number of the two strands is fixed by the initial X and u
+ * (required, at least 6 base pairs).  Molecules never interact with each
+ * other. */
 typedef struct dsdna_system {
   int n_mol;
   const int* n_bp;       /* [n_mol], each >= 1 */
@@ -141,6 +150,7 @@ typedef struct dsdna_system {
   const double* Om;      /* [3*n_nt] or NULL (with V) */
   const int* tether;     /* [n_mol] or NULL */
   const signed char* gc; /* [n_bp total] 1 = G.C pair (stiffness K2_gc), 0 = A.T (K2), or NULL: all A.T */
+  const int* circular;   /* [n_mol] or NULL (all linear) */
 } dsdna_system;
 
 /* Device allocator used for every buffer of a context.  NULL: cudaMalloc/cudaFree. */
@@ -153,9 +163,11 @@ typedef struct dsdna_allocator {
 typedef struct dsdna_obs {
   double rz;        /* extension along z of the base-pair centres (Sec. 4.1) */
   double denat;     /* fraction of base pairs with broken hydrogen bond (Sec. 5) */
-  double tw;        /* twist in turns, sum of (alpha + gamma) / 2 pi (Sec. 3.2, App. B) */
-  double tw_ideal;  /* twist of the relaxed helix of the same length: (N-2) steps x 36 deg */
-  double lk;        /* linking number of the closed strands (App. C Eq. 17) */
+  double tw;        /* twist in turns, sum of (alpha + gamma) / 2 pi (Sec. 3.2, App. B);
+                       N - 2 increments on a linear molecule, N on a ring */
+  double tw_ideal;  /* twist of the relaxed helix of the same length: (N-2) (ring: N) x 36 deg */
+  double lk;        /* linking number of the closed strands (App. C Eq. 17): a linear
+                       molecule's strands closed far away (App. C), a ring's as they are */
   double wr;        /* writhe lk - tw (Sec. 4.2, Eq. 6) */
 } dsdna_obs;
 
@@ -234,6 +246,14 @@ int dsdna_get_state(dsdna_ctx* ctx, int mol, double* X, double* V, double* u, do
  * leaves that field unchanged); clears a poisoned context and forces a
  * neighbour-list rebuild. */
 int dsdna_set_state(dsdna_ctx* ctx, int mol, const double* X, const double* V, const double* u, const double* Om);
+
+/* Bubble rule 2 mask of molecule mol (-1: all), one byte per nucleotide slot:
+ * bit 0 = dihedral of the step to the next nucleotide removed, bit 1 =
+ * bending centred on the nucleotide removed (Sec. 5).  get synchronises and
+ * copies to a caller-owned host array; set installs one (entries 0..3; NULL
+ * clears), e.g. with the state of a checkpoint. */
+int dsdna_get_bubble_mask(dsdna_ctx* ctx, int mol, unsigned char* mask);
+int dsdna_set_bubble_mask(dsdna_ctx* ctx, int mol, const unsigned char* mask);
 
 /* Conservative site forces (bead, patch) on every nucleotide at the current
  * state, including the applied loads, as FP64 host arrays [3*n_nt] each. */

@@ -141,11 +141,15 @@ static int64_t prev_nt(const topo_t* t, int64_t g) {
   return nt_at(t, m, (g & 1) == 0 ? k - 1 : k + 1, g);
 }
 /* Sec. 2 / Fig. 1d: along each strand one sterically interacting bead is
- * followed by two ghost beads; the index is counted 5'->3'. */
+ * followed by two ghost beads; the index q is counted 5'->3'.  On a ring
+ * whose length is not a multiple of 3 the last steric bead before the
+ * junction would sit fewer than 3 nucleotides from the first one after it
+ * (gap N - q + phase): it is a ghost instead, leaving one gap of 4 or 5. */
 static int is_steric(const or_params* p, const topo_t* t, int64_t g) {
   int m = mol_of(t, g); int64_t k = g / 2 - t->off[m]; int N = t->n_bp[m];
   int64_t q = ((g & 1) == 0) ? k : (N - 1 - k);
-  return (int)(q % 3) == p->steric_phase;
+  if ((int)(q % 3) != p->steric_phase) return 0;
+  return !(is_ring(t, m) && q > N + p->steric_phase - 3);
 }
 
 /* site position: site 0 = bead, 1 = patch (Sec. 2) */

@@ -40,6 +40,7 @@ struct dsdna_ctx {
   std::vector<int> n_bp;
   std::vector<int64_t> off;      // bp offsets [n_mol + 1]
   std::vector<int> tether;
+  std::vector<int> circular;     // per molecule: 1 = ring
   std::vector<double> ext;       // [n_mol][8]
   int64_t n = 0;
   int64_t ns = 0;                // row stride of the [component][slot] arrays (n rounded up to 32)
@@ -50,6 +51,10 @@ struct dsdna_ctx {
   double* X = nullptr; double* V = nullptr; void* Om = nullptr;
   int4* Kw = nullptr; float4* U = nullptr; double* ud = nullptr;
   int* topo = nullptr; int* img = nullptr; int* kref = nullptr; int* nbr = nullptr; int* ncnt = nullptr;
+  int64_t n_junc = 0;            // junction owners of circular molecules (8 per ring)
+  // kernel instance: with circular molecules or the bubble rule, MODE_EXT
+  int kernel_ext() const { return (n_junc > 0 || p.bubble_rule > 0) ? MODE_EXT : 0; }
+  int64_t* jslot = nullptr; int* jidx = nullptr; void* jout = nullptr;
   unsigned* cnt = nullptr; unsigned* start = nullptr; int* key = nullptr;
   float4* cent = nullptr; float4* wpos = nullptr; unsigned* bsum = nullptr;
   int64_t* mol_off = nullptr; double* ext_d = nullptr;
@@ -304,7 +309,8 @@ static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
   fill_coef(c->p, a.c);
   a.n = c->n; a.ns = c->ns; a.n_mol = c->n_mol; a.nseg = (c->n + SEG_SLOTS - 1) / SEG_SLOTS; a.cap = c->p.max_neighbors;
   a.nsteps = 0; a.noise_mode = c->p.noise;
-  a.bubble = c->p.bubble_rule ? 1 : 0;
+  a.bubble = c->p.bubble_rule;
+  a.n_junc = c->n_junc; a.jslot = c->jslot; a.jidx = c->jidx; a.jout = (Real*)c->jout;
   a.seed_lo = (uint32_t)c->p.seed; a.seed_hi = (uint32_t)(c->p.seed >> 32);
   a.spin_budget = 4000000000ull;
   a.X = c->X; a.V = c->V; a.Om = (Real*)c->Om; a.Kw = c->Kw; a.U = c->U; a.ud = c->ud;
@@ -329,7 +335,7 @@ static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
 
 static int validate(const dsdna_params* p, const dsdna_system* s) {
   if (!p || !s || s->n_mol < 1 || !s->n_bp) return fail(nullptr, DSDNA_EINVAL, "params/system missing or n_mol < 1");
-  if (s->n_mol >= (1 << 23)) return fail(nullptr, DSDNA_EINVAL, "too many molecules");
+  if (s->n_mol >= (1 << (31 - MOL_SHIFT))) return fail(nullptr, DSDNA_EINVAL, "too many molecules (at most 2^21)");
   int64_t tot = 0;
   for (int m = 0; m < s->n_mol; ++m) {
     if (s->n_bp[m] < 1) return fail(nullptr, DSDNA_EINVAL, "molecule with fewer than one base pair");
@@ -342,7 +348,7 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
   if (!(p->dt > 0.0) || !(p->mass > 0.0) || !(p->ell > 0.0) || !(p->R0 > 0.0) || !(p->rc_hb > 0.0) || p->gamma < 0.0 || p->kT < 0.0)
     return fail(nullptr, DSDNA_EINVAL, "non-positive dt/mass/ell/R0/rc or negative gamma/kT");
   if (p->precision != DSDNA_PREC_MIXED && p->precision != DSDNA_PREC_FP64) return fail(nullptr, DSDNA_EINVAL, "precision");
-  if (p->bubble_rule != 0 && p->bubble_rule != 1) return fail(nullptr, DSDNA_EINVAL, "bubble_rule must be 0 or 1");
+  if (p->bubble_rule < 0 || p->bubble_rule > 2) return fail(nullptr, DSDNA_EINVAL, "bubble_rule must be 0, 1 or 2");
   if (p->K2_gc < 0.0) return fail(nullptr, DSDNA_EINVAL, "K2_gc must be >= 0");
   if (p->noise < 0 || p->noise > 2) return fail(nullptr, DSDNA_EINVAL, "noise mode");
   if (p->skin < 0.0 || p->skin > 1.0) return fail(nullptr, DSDNA_EINVAL, "skin must be in [0, 1] nm");
@@ -350,6 +356,12 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
   if (p->block_threads && (p->block_threads < 64 || p->block_threads > 256 || p->block_threads % 32))
     return fail(nullptr, DSDNA_EINVAL, "block_threads must be a multiple of 32 in [64, 256]");
   if ((s->X == nullptr) != (s->u == nullptr)) return fail(nullptr, DSDNA_EINVAL, "X and u must be given together");
+  if (s->circular)
+    for (int m = 0; m < s->n_mol; ++m)
+      if (s->circular[m]) {
+        if (s->n_bp[m] < 6) return fail(nullptr, DSDNA_EINVAL, "a circular molecule needs at least 6 base pairs");
+        if (!s->X) return fail(nullptr, DSDNA_EINVAL, "circular molecules need an initial X and u");
+      }
   if ((s->V == nullptr) != (s->Om == nullptr)) return fail(nullptr, DSDNA_EINVAL, "V and Om must be given together");
   return DSDNA_OK;
 }
@@ -411,6 +423,8 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   c->n = 2 * c->off[c->n_mol];
   c->tether.assign(c->n_mol, 0);
   if (sys->tether) for (int m = 0; m < c->n_mol; ++m) c->tether[m] = sys->tether[m] ? 1 : 0;
+  c->circular.assign(c->n_mol, 0);
+  if (sys->circular) for (int m = 0; m < c->n_mol; ++m) c->circular[m] = sys->circular[m] ? 1 : 0;
   c->ext.assign((size_t)c->n_mol * 8, 0.0);
   const int64_t n = c->n;
   c->nseg = (n + c->T - 1) / c->T;
@@ -463,6 +477,12 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   if (!c->Om) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: Om"));
   if (f64) { ALLOC(ud, double, 6 * ns); } else { ALLOC(Kw, int4, 2 * ns); ALLOC(U, float4, 2 * ns); }
   ALLOC(topo, int, ns); ALLOC(img, int, ns); ALLOC(kref, int, 3 * ns);
+  for (int m = 0; m < c->n_mol; ++m) c->n_junc += c->circular[m] ? 8 : 0;
+  if (c->n_junc) {
+    ALLOC(jslot, int64_t, c->n_junc); ALLOC(jidx, int, ns);
+    c->jout = dalloc(c, (f64 ? 8 : 4) * 16 * (size_t)c->n_junc);
+    if (!c->jout) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: jout"));
+  }
   ALLOC(nbr, int, (size_t)c->p.max_neighbors * ns); ALLOC(ncnt, int, ns);
   ALLOC(cnt, unsigned, c->H); ALLOC(start, unsigned, (size_t)c->H + 1); ALLOC(key, int, nn);
   ALLOC(cent, float4, nn); ALLOC(wpos, float4, nn);
@@ -482,8 +502,9 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
   for (int mode = 0; mode < 3; ++mode) {
     int bps = 0;
-    cudaError_t e = f64 ? engine_occupancy<double>(mode, c->T, &bps, &c->smem[mode])
-                        : engine_occupancy<float>(mode, c->T, &bps, &c->smem[mode]);
+    const int m = mode | c->kernel_ext();
+    cudaError_t e = f64 ? engine_occupancy<double>(m, c->T, &bps, &c->smem[mode])
+                        : engine_occupancy<float>(m, c->T, &bps, &c->smem[mode]);
     if (e != cudaSuccess || bps < 1) return bad(fail(c, DSDNA_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e)));
     if (c->p.blocks_per_sm > 0) bps = std::min(bps, c->p.blocks_per_sm);
     c->grid[mode] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * nsm, c->nseg));
@@ -500,17 +521,45 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
       for (int s = 0; s < 2; ++s) {
         const int64_t g = 2 * (c->off[m] + k) + s;
         const int q = s == 0 ? k : N - 1 - k;     // index along the strand from its 5' end
+        const bool ring = c->circular[m] != 0;     // Sec. 6 rings: the last nucleotide bonds to the first
+        const int ph = c->p.steric_phase;
         int f = 0;
-        if (q % 3 == c->p.steric_phase) f |= F_STERIC;
+        // on a ring the last steric bead before the junction turns ghost when it
+        // would sit fewer than 3 nucleotides from the first one after it
+        if (q % 3 == ph && !(ring && q > N + ph - 3)) f |= F_STERIC;
+        // a ring's neighbour across the junction is reached through the
+        // junction table, not the slot-order ring of the step kernel: its
+        // F_PREV / F_NEXT stays clear
         if (q > 0) f |= F_PREV;
         if (q < N - 1) f |= F_NEXT;
+        if (ring && (k < 2 || k > N - 3)) f |= F_JUNC;
         if (c->tether[m] && k == 0) f |= F_FROZEN;
         if (k == N - 1) f |= F_TOP;
         if (sys->gc && sys->gc[c->off[m] + k]) f |= F_GC;   // Sec. 5: G.C pair, stiffer hydrogen bond
-        topo[g] = f | (m << 8);
+        topo[g] = f | (m << MOL_SHIFT);
       }
   }
   auto cpy = [&](void* dst, const void* src, size_t b) { return cudaMemcpy(dst, src, b, cudaMemcpyHostToDevice); };
+  if (c->n_junc) {
+    // junction owners of ring r: base pairs 0, 1, N-2, N-1 (position p), both strands: entry 8 r + 2 p + s
+    std::vector<int64_t> js((size_t)c->n_junc);
+    std::vector<int> ji(ns, -1);
+    int64_t t = 0;
+    for (int m = 0; m < c->n_mol; ++m) {
+      if (!c->circular[m]) continue;
+      const int N = c->n_bp[m];
+      const int ks[4] = {0, 1, N - 2, N - 1};
+      for (int p4 = 0; p4 < 4; ++p4)
+        for (int s = 0; s < 2; ++s, ++t) {
+          const int64_t g = 2 * (c->off[m] + ks[p4]) + s;
+          js[(size_t)t] = g;
+          ji[(size_t)g] = (int)t;
+        }
+    }
+    if (cpy(c->jslot, js.data(), sizeof(int64_t) * js.size()) != cudaSuccess ||
+        cpy(c->jidx, ji.data(), sizeof(int) * ns) != cudaSuccess)
+      return bad(fail(c, DSDNA_ECUDA, "junction table upload"));
+  }
   if (cpy(c->topo, topo.data(), sizeof(int) * ns) != cudaSuccess ||
       cpy(c->mol_off, c->off.data(), sizeof(int64_t) * (c->n_mol + 1)) != cudaSuccess ||
       cpy(c->ext_d, c->ext.data(), sizeof(double) * c->ext.size()) != cudaSuccess)
@@ -593,11 +642,11 @@ static cudaError_t launch_engine(dsdna_ctx* c, int mode, int64_t nsteps, int64_t
   if (c->fp64()) {
     KArgs<double> a = c->kd;
     a.nsteps = nsteps; a.steps_left = steps_left; a.use_cond = use_cond; a.h_while = hw;
-    return engine_launch<double>(mode, a, c->grid[mode], c->T, c->smem[mode], c->st);
+    return engine_launch<double>(mode | c->kernel_ext(), a, c->grid[mode], c->T, c->smem[mode], c->st);
   }
   KArgs<float> a = c->kf;
   a.nsteps = nsteps; a.steps_left = steps_left; a.use_cond = use_cond; a.h_while = hw;
-  return engine_launch<float>(mode, a, c->grid[mode], c->T, c->smem[mode], c->st);
+  return engine_launch<float>(mode | c->kernel_ext(), a, c->grid[mode], c->T, c->smem[mode], c->st);
 }
 
 // force / energy pass on a fresh list
@@ -849,6 +898,7 @@ extern "C" int dsdna_observables(dsdna_ctx* c, int mol, unsigned flags, dsdna_ob
   a.ud = c->fp64() ? c->ud + (size_t)cur * 3 * c->ns : nullptr;
   a.g0 = 2 * c->off[mol];
   a.N = c->n_bp[mol];
+  a.ring = c->circular[mol];
   a.h = 0.5 * c->p.ell;
   a.rc2 = c->p.rc_hb * c->p.rc_hb;
   a.mid = c->obs_scratch;
@@ -862,7 +912,9 @@ extern "C" int dsdna_observables(dsdna_ctx* c, int mol, unsigned flags, dsdna_ob
   out->rz = o[0];
   out->denat = o[1] / (double)a.N;
   out->tw = o[2];
-  out->tw_ideal = a.N >= 3 ? (double)(a.N - 2) * (c->p.d_dih + M_PI) / (2.0 * M_PI) : 0.0;
+  // twist increments: N on a ring (the last step closes it), N - 2 on a linear molecule
+  const int ninc = a.ring ? a.N : a.N - 2;
+  out->tw_ideal = a.N >= 3 ? (double)ninc * (c->p.d_dih + M_PI) / (2.0 * M_PI) : 0.0;
   out->lk = (flags & DSDNA_OBS_LK) ? o[4] : 0.0;
   out->wr = (flags & DSDNA_OBS_LK) ? o[4] - o[2] : 0.0;
   return DSDNA_OK;
@@ -907,6 +959,36 @@ extern "C" int dsdna_set_state(dsdna_ctx* c, int mol, const double* X, const dou
   const int64_t g0 = mol < 0 ? 0 : 2 * c->off[mol];
   const int64_t cnt = mol < 0 ? c->n : 2 * (int64_t)c->n_bp[mol];
   return upload_state(c, g0, cnt, X, V, u, Om);
+}
+
+// The rule 2 mask lives in bits RM_SHIFT.. of the device topology words.
+extern "C" int dsdna_get_bubble_mask(dsdna_ctx* c, int mol, unsigned char* mask) {
+  if (!c || !mask) return DSDNA_EINVAL;
+  if (mol < -1 || mol >= c->n_mol) return fail(c, DSDNA_EINVAL, "molecule index out of range");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  const int64_t g0 = mol < 0 ? 0 : 2 * c->off[mol];
+  const int64_t cnt = mol < 0 ? c->n : 2 * (int64_t)c->n_bp[mol];
+  std::vector<int> t((size_t)cnt);
+  CK(cudaMemcpy(t.data(), c->topo + g0, sizeof(int) * (size_t)cnt, cudaMemcpyDeviceToHost), "read bubble mask");
+  for (int64_t i = 0; i < cnt; ++i) mask[i] = (unsigned char)((t[(size_t)i] >> RM_SHIFT) & 3);
+  return DSDNA_OK;
+}
+
+extern "C" int dsdna_set_bubble_mask(dsdna_ctx* c, int mol, const unsigned char* mask) {
+  if (!c) return DSDNA_EINVAL;
+  if (mol < -1 || mol >= c->n_mol) return fail(c, DSDNA_EINVAL, "molecule index out of range");
+  const int64_t g0 = mol < 0 ? 0 : 2 * c->off[mol];
+  const int64_t cnt = mol < 0 ? c->n : 2 * (int64_t)c->n_bp[mol];
+  if (mask)
+    for (int64_t i = 0; i < cnt; ++i)
+      if (mask[i] > 3) return fail(c, DSDNA_EINVAL, "bubble mask entries must be in 0..3");
+  CK(cudaStreamSynchronize(c->st), "synchronize");
+  std::vector<int> t((size_t)cnt);
+  CK(cudaMemcpy(t.data(), c->topo + g0, sizeof(int) * (size_t)cnt, cudaMemcpyDeviceToHost), "read topology");
+  for (int64_t i = 0; i < cnt; ++i)
+    t[(size_t)i] = (t[(size_t)i] & ~(3 << RM_SHIFT)) | ((mask ? (int)mask[i] : 0) << RM_SHIFT);
+  CK(cudaMemcpy(c->topo + g0, t.data(), sizeof(int) * (size_t)cnt, cudaMemcpyHostToDevice), "write bubble mask");
+  return DSDNA_OK;
 }
 
 extern "C" int dsdna_compute_forces(dsdna_ctx* c, double* Fb, double* Fp) {

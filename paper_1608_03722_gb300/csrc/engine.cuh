@@ -22,7 +22,16 @@
 namespace dsdna {
 
 // ---------------------------------------------------------------- constants
-enum : int { F_STERIC = 1, F_PREV = 2, F_NEXT = 4, F_FROZEN = 8, F_TOP = 16, F_GC = 32 };
+// Topology flags of a slot (bits 0-7; the molecule index sits above bit 8).
+// F_GC: G.C base pair (Sec. 5).  F_JUNC: base pair 0, 1, N-2 or N-1 of a
+// circular molecule, whose neighbourhood crosses the junction.  Bit 6 is
+// used by the step kernel's shared copy of the flags only.
+enum : int { F_STERIC = 1, F_PREV = 2, F_NEXT = 4, F_FROZEN = 8, F_TOP = 16, F_GC = 32, F_JUNC = 128 };
+// Bits 8-9: terms removed by bubble rule 2 (bit 8 the dihedral of the step to
+// the next nucleotide, bit 9 the bending centred on the slot), set by the step
+// kernel.  The molecule index starts at bit MOL_SHIFT.
+constexpr int RM_SHIFT = 8;
+constexpr int MOL_SHIFT = 10;
 // Cell table: periodic box with >= 3 cells per edge -> linear index (x fastest;
 // the three x-neighbours of a cell are consecutive entries); smaller periodic
 // box -> Morton index; open box -> hash of (molecule, cell).
@@ -32,6 +41,7 @@ enum : unsigned {
 };
 constexpr unsigned B_ERRMASK = B_EFENE | B_ENAN | B_EOVF | B_ETIMEOUT | B_EIMG;
 enum : int { MODE_STEP = 0, MODE_FORCES = 1, MODE_ENERGY = 2 };
+constexpr int MODE_EXT = 4;   // launch flag: kernel instance with circular molecules / bubble rule
 constexpr int NTERMS = 10;
 constexpr int EOUT_STRIDE = 16;           // energy terms + 6 virial
 constexpr float FIX_SCALE_F = 1.0f / 536870912.0f;  // 2^-29
@@ -85,7 +95,7 @@ struct KArgs {
   int64_t n;
   int64_t ns;      // row stride of the [component][slot] arrays: n rounded up to a multiple of 32
   int n_mol;
-  int bubble;      // 1: no dihedral / bending inside runs of > 2 open base pairs (Sec. 5)
+  int bubble;      // no dihedral / bending inside runs of > 2 open base pairs (Sec. 5): 0 off, 1 while, 2 for good
   int64_t nseg;
   int cap;
   int64_t nsteps;
@@ -100,11 +110,16 @@ struct KArgs {
   int4* Kw;        // mixed: [2][n] fixed-point mirror (w = packed image)
   float4* U;       // mixed: [2][n] orientation (w unused)
   double* ud;      // fp64: [2][3][n] orientation
-  const int* topo; // [n] flags | mol << 8
+  int* topo;       // [n] flags | removed << RM_SHIFT | mol << MOL_SHIFT
   int* img;        // [n] packed image (both modes)
   int* kref;       // [3][n] mirror at the last build
   int* nbr;        // [cap][n] list entries (ent_make)
   int* ncnt;       // [n]
+  // circular molecules: junction owners (8 per ring)
+  int64_t n_junc;
+  const int64_t* jslot;  // [n_junc] slot of each junction owner
+  const int* jidx;       // [n] junction entry of a F_JUNC slot
+  Real* jout;            // [n_junc][16] their forces: sb, sp, nb, np, pp
   // cell hash
   unsigned* cnt;   // [H]
   unsigned* start; // [H + 1]

@@ -71,73 +71,204 @@ __device__ __forceinline__ void mark_open(const KArgs<Real>& a, const SegSmem<Re
 }
 __device__ __forceinline__ bool bp_open(const int* flg, int64_t k, int mol) {
   const int fa = flg[ring(2 * k)];
-  return (fa & F_OPEN) && (fa >> 8) == mol;
+  return (fa & F_OPEN) && (fa >> MOL_SHIFT) == mol;
 }
 
-// Bonded terms owned by slot o (ring index ri): the step o -> next along its
-// strand (FENE + WCA, Morse, dihedral, planarity) and the bending angle at o.
-// Forces go to the owner (cs), its next nucleotide (cn) and the previous
-// patch (cp), so each term is evaluated once.  With the bubble rule (Sec. 5)
-// the dihedral is left out when both base pairs of the step lie in a run of
-// three or more open pairs, and the bending when the pairs of o and of both
-// its strand neighbours are open; the ring then holds base pairs o/2 - 2 ..
-// o/2 + 2.
+// Forces of the terms one owner evaluates: on the owner's bead and patch
+// (sb, sp), on its next nucleotide (nb, np) and on its previous patch (pp).
 template <class Real>
-__device__ __forceinline__ void owner_terms(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t o, unsigned& fl,
-                                            Real* E, Real* W) {
+struct OwnerOut {
+  V3<Real> sb, sp, nb, np, pp;
+};
+
+// Where an owner's neighbourhood comes from.  RingSrc: the warp's shared
+// ring (every owner whose base pairs o/2 - 2 .. o/2 + 2 are consecutive slots
+// of its molecule).  GlobalSrc: global memory with the indices of a circular
+// molecule taken modulo its length (owners next to the junction of a ring,
+// and the far owners a junction nucleotide re-evaluates).
+template <class Real>
+struct RingSrc {
+  const SPos<Real>* spos;
+  const int* flg;
+  __device__ __forceinline__ SPos<Real> pos(int64_t g) const { return spos[ring(g)]; }
+  __device__ __forceinline__ int64_t step(int64_t g, int d) const { return g + d; }
+  __device__ __forceinline__ bool open(int64_t k, int mol) const { return bp_open(flg, k, mol); }
+};
+template <class Real>
+struct GlobalSrc {
+  const KArgs<Real>& a;   // the kernel's __grid_constant__ parameters
+  int cur;
+  int64_t off, N;   // base-pair offset and length of the owner's molecule
+  __device__ __forceinline__ int64_t wrap(int64_t k) const {
+    int64_t r = (k - off) % N;
+    return off + (r < 0 ? r + N : r);
+  }
+  __device__ __forceinline__ SPos<Real> pos(int64_t g) const {
+    SPos<Real> s;
+    load_slot(a, cur, g, s);
+    return s;
+  }
+  __device__ __forceinline__ int64_t step(int64_t g, int d) const { return 2 * wrap((g >> 1) + d / 2) + (g & 1); }
+  __device__ __forceinline__ bool open(int64_t k, int /*mol*/) const {
+    k = wrap(k);
+    const SPos<Real> pa = pos(2 * k), pb = pos(2 * k + 1);
+    const V3<Real> d = rel(pa, pb) + a.c.h * (uvec(pb) - uvec(pa));
+    return dot(d, d) > a.c.rchb2;
+  }
+};
+
+// Bonded terms owned by slot o with flags f: the step o -> next along its
+// strand (FENE + WCA, Morse, dihedral, planarity) and the bending angle at o,
+// each evaluated once.  Bubble rule (Sec. 5): the dihedral is left out when
+// both base pairs of the step lie in a run of three or more open pairs, and
+// the bending when the pairs of o and of both its strand neighbours are open;
+// rule 2 also leaves out what the slot's removed bits (RM_SHIFT) mark and,
+// when `persist`, adds what it left out to them.
+// Terms of owner o that the bubble rule leaves out: bit 0 the dihedral, bit 1
+// the bending.  Out of line: it runs only with the rule on, and the step
+// kernel's common path keeps its registers.
+template <class Real, class Src>
+__device__ __noinline__ unsigned bubble_bits(const KArgs<Real>& a, const Src src, int64_t o, int f, bool persist) {
+  const unsigned r0 = (unsigned)(f >> RM_SHIFT) & 3u;   // set by rule 2 only
+  const int mol = f >> MOL_SHIFT, st = (o & 1) ? -1 : 1;
+  const int64_t ko = o >> 1;
+  unsigned r1 = r0;
+  if (src.open(ko, mol) && src.open(ko + st, mol)) {
+    const bool before = src.open(ko - st, mol);
+    if (before || src.open(ko + 2 * st, mol)) r1 |= 1u;
+    if ((f & F_PREV) && before) r1 |= 2u;
+  }
+  if (persist && r1 != r0) atomicOr(a.topo + o, (int)(r1 << RM_SHIFT));
+  return r1;
+}
+
+template <class Real, bool EXT, class Src>
+__device__ __forceinline__ void owner_eval(const KArgs<Real>& a, const Src& src, int64_t o, int f, bool persist,
+                                           unsigned& fl, Real* E, Real* W, OwnerOut<Real>& out) {
+  const int dir = (o & 1) ? -2 : 2;   // strand A (even slot) runs up, strand B down
+  unsigned rm = 0u;
+  if constexpr (EXT) rm = a.bubble ? bubble_bits(a, src, o, f, persist) : 0u;
+  const bool skip_dih = (rm & 1u) != 0, skip_bend = (rm & 2u) != 0;
+  const SPos<Real> so = src.pos(o);
+  const SPos<Real> sq = src.pos(src.step(o, dir));
+  const Real h = a.c.h;
+  const V3<Real> uo = uvec(so), uq = uvec(sq);
+  const V3<Real> Rq = rel(so, sq);
+  const V3<Real> bo = -h * uo, po = h * uo, bq = Rq - h * uq, pq = Rq + h * uq;
+  // FENE + WCA, Morse
+  V3<Real> fb = t_fene(a.c, bq - bo, fl, E);
+  out.nb += fb; out.sb -= fb;
+  V3<Real> fm = t_morse(a.c, pq - po, E);
+  out.np += fm; out.sp -= fm;
+  if (W) { vir_add(W, bq - bo, fb); vir_add(W, pq - po, fm); }
+  // dihedral A-E-F-B = bead o, patch o, patch q, bead q
+  if (!skip_dih) {
+    V3<Real> fA, fE, fF, fB;
+    t_dihedral(a.c, bo, po, pq, bq, fA, fE, fF, fB, E);
+    out.sb += fA; out.sp += fE; out.np += fF; out.nb += fB;
+    if (W) { vir_add(W, bo, fA); vir_add(W, po, fE); vir_add(W, pq, fF); vir_add(W, bq, fB); }
+  }
+  // planarity: vertex patch q between patch o and bead q
+  V3<Real> f1, f2;
+  t_planar(a.c, po - pq, bq - pq, f1, f2, E);
+  out.sp += f1; out.nb += f2; out.np -= (f1 + f2);
+  if (W) { vir_add(W, po, f1); vir_add(W, bq, f2); vir_add(W, pq, -(f1 + f2)); }
+  if ((f & F_PREV) && !skip_bend) {
+    const SPos<Real> sr = src.pos(src.step(o, -dir));
+    const V3<Real> pr = rel(so, sr) + h * uvec(sr);
+    V3<Real> g1, g2;
+    t_bend(a.c, pr - po, pq - po, g1, g2, E);
+    out.pp += g1; out.np += g2; out.sp -= (g1 + g2);
+    if (W) { vir_add(W, pr, g1); vir_add(W, pq, g2); vir_add(W, po, -(g1 + g2)); }
+  }
+}
+
+template <class Real>
+__device__ __forceinline__ void store_owner(const SegSmem<Real>& sm, int ri, const OwnerOut<Real>& out) {
+  sm.cs[0 * RING + ri] = out.sb.x; sm.cs[1 * RING + ri] = out.sb.y; sm.cs[2 * RING + ri] = out.sb.z;
+  sm.cs[3 * RING + ri] = out.sp.x; sm.cs[4 * RING + ri] = out.sp.y; sm.cs[5 * RING + ri] = out.sp.z;
+  sm.cn[0 * RING + ri] = out.nb.x; sm.cn[1 * RING + ri] = out.nb.y; sm.cn[2 * RING + ri] = out.nb.z;
+  sm.cn[3 * RING + ri] = out.np.x; sm.cn[4 * RING + ri] = out.np.y; sm.cn[5 * RING + ri] = out.np.z;
+  sm.cp[0 * RING + ri] = out.pp.x; sm.cp[1 * RING + ri] = out.pp.y; sm.cp[2 * RING + ri] = out.pp.z;
+}
+
+// Junction owners of circular molecules (base pairs 0, 1, N-2, N-1, both
+// strands; entry t = 8 r + 2 p + strand for ring r and position p), all
+// evaluated from global memory at the start of a step, before a grid
+// barrier: their forces go to a.jout ([16] per entry: sb, sp, nb, np, pp),
+// which the strip pass reads for these owners and for the two nucleotides of
+// each strand whose neighbour owner lies across the junction.  MODE_ENERGY
+// adds their energies here; MODE_STEP records removed terms (rule 2).
+template <class Real, int MODE>
+__device__ unsigned junction_pass(const KArgs<Real>& a, int cur) {
+  unsigned fl = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_junc; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = a.jslot[t];
+    const int f = a.topo[o] | F_PREV | F_NEXT;   // both neighbours exist on a ring
+    const int mol = f >> MOL_SHIFT;
+    const int64_t off = a.mol_off[mol];
+    const GlobalSrc<Real> src{a, cur, off, a.mol_off[mol + 1] - off};
+    OwnerOut<Real> out{{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if constexpr (MODE == MODE_ENERGY) {
+      Real E[NTERMS], W[6];
+      for (int k = 0; k < NTERMS; ++k) E[k] = 0;
+      for (int k = 0; k < 6; ++k) W[k] = 0;
+      owner_eval<Real, true>(a, src, o, f, false, fl, E, W, out);
+      flush_energy(a, mol, E, W);
+    } else {
+      owner_eval<Real, true>(a, src, o, f, MODE == MODE_STEP, fl, (Real*)nullptr, (Real*)nullptr, out);
+    }
+    Real* j = a.jout + 16 * t;
+    const V3<Real> v[5] = {out.sb, out.sp, out.nb, out.np, out.pp};
+    for (int q = 0; q < 5; ++q) { j[3 * q] = v[q].x; j[3 * q + 1] = v[q].y; j[3 * q + 2] = v[q].z; }
+  }
+  return fl;
+}
+
+template <class Real>
+__device__ __forceinline__ V3<Real> jvec(const KArgs<Real>& a, int t, int q) {
+  const Real* j = a.jout + 16 * (int64_t)t + 3 * q;
+  return V3<Real>{j[0], j[1], j[2]};
+}
+
+// A junction owner's forces from a.jout into its ring entries.  Nucleotide o
+// is the first (position 0 on strand A, 3 on strand B) or last of its strand
+// in slot order: the owner across the junction (entry ta) is its previous
+// one, whose next-nucleotide forces it takes, or its next one, whose
+// previous-patch force it takes.  Its slot flags have that neighbour's
+// F_PREV / F_NEXT cleared, so the ring gather of nucleotide_pass skips it.
+// Out of line: rings are rare.
+template <class Real>
+__device__ __noinline__ void junction_copy(const KArgs<Real>& a, Real* cs, Real* cn, Real* cp, int64_t o) {
+  const int t = a.jidx[o], pos = (t >> 1) & 3, ta = (t & ~7) | ((3 - pos) << 1) | (t & 1);
+  OwnerOut<Real> out{jvec(a, t, 0), jvec(a, t, 1), jvec(a, t, 2), jvec(a, t, 3), jvec(a, t, 4)};
+  const bool first = (o & 1) ? pos == 3 : pos == 0, last = (o & 1) ? pos == 0 : pos == 3;
+  if (first) { out.sb += jvec(a, ta, 2); out.sp += jvec(a, ta, 3); }
+  if (last) out.sp += jvec(a, ta, 4);
+  const int ri = ring(o);
+  cs[0 * RING + ri] = out.sb.x; cs[1 * RING + ri] = out.sb.y; cs[2 * RING + ri] = out.sb.z;
+  cs[3 * RING + ri] = out.sp.x; cs[4 * RING + ri] = out.sp.y; cs[5 * RING + ri] = out.sp.z;
+  cn[0 * RING + ri] = out.nb.x; cn[1 * RING + ri] = out.nb.y; cn[2 * RING + ri] = out.nb.z;
+  cn[3 * RING + ri] = out.np.x; cn[4 * RING + ri] = out.np.y; cn[5 * RING + ri] = out.np.z;
+  cp[0 * RING + ri] = out.pp.x; cp[1 * RING + ri] = out.pp.y; cp[2 * RING + ri] = out.pp.z;
+}
+
+// Owner o's terms into the ring entries of o (cs, cn, cp).  EXT: the kernel
+// instance for systems with circular molecules or the bubble rule.
+template <class Real, bool EXT>
+__device__ __forceinline__ void owner_terms(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t o, int cur,
+                                            bool persist, unsigned& fl, Real* E, Real* W) {
   const int ri = ring(o);
   const int f = sm.flg[ri];
-  V3<Real> sb{0, 0, 0}, sp{0, 0, 0}, nb{0, 0, 0}, np{0, 0, 0}, pp{0, 0, 0};
-  if (f & F_NEXT) {
-    const int dir = (o & 1) ? -2 : 2;   // strand A (even slot) runs up, strand B down
-    bool skip_dih = false, skip_bend = false;
-    if (a.bubble) {
-      const int mol = f >> 8;
-      const int64_t ko = o >> 1, kq = (o + dir) >> 1;
-      if (bp_open(sm.flg, ko, mol) && bp_open(sm.flg, kq, mol)) {
-        const int64_t lo = ko < kq ? ko : kq, hi = ko < kq ? kq : ko;
-        skip_dih = bp_open(sm.flg, lo - 1, mol) || bp_open(sm.flg, hi + 1, mol);
-        skip_bend = (f & F_PREV) && bp_open(sm.flg, (o - dir) >> 1, mol);
-      }
-    }
-    const SPos<Real> so = sm.pos[ri];
-    const SPos<Real> sq = sm.pos[ring(o + dir)];
-    const Real h = a.c.h;
-    const V3<Real> uo = uvec(so), uq = uvec(sq);
-    const V3<Real> Rq = rel(so, sq);
-    const V3<Real> bo = -h * uo, po = h * uo, bq = Rq - h * uq, pq = Rq + h * uq;
-    // FENE + WCA, Morse
-    V3<Real> fb = t_fene(a.c, bq - bo, fl, E);
-    nb += fb; sb -= fb;
-    V3<Real> fm = t_morse(a.c, pq - po, E);
-    np += fm; sp -= fm;
-    if (W) { vir_add(W, bq - bo, fb); vir_add(W, pq - po, fm); }
-    // dihedral A-E-F-B = bead o, patch o, patch q, bead q
-    if (!skip_dih) {
-      V3<Real> fA, fE, fF, fB;
-      t_dihedral(a.c, bo, po, pq, bq, fA, fE, fF, fB, E);
-      sb += fA; sp += fE; np += fF; nb += fB;
-      if (W) { vir_add(W, bo, fA); vir_add(W, po, fE); vir_add(W, pq, fF); vir_add(W, bq, fB); }
-    }
-    // planarity: vertex patch q between patch o and bead q
-    V3<Real> f1, f2;
-    t_planar(a.c, po - pq, bq - pq, f1, f2, E);
-    sp += f1; nb += f2; np -= (f1 + f2);
-    if (W) { vir_add(W, po, f1); vir_add(W, bq, f2); vir_add(W, pq, -(f1 + f2)); }
-    if ((f & F_PREV) && !skip_bend) {
-      const SPos<Real> sr = sm.pos[ring(o - dir)];
-      const V3<Real> pr = rel(so, sr) + h * uvec(sr);
-      V3<Real> g1, g2;
-      t_bend(a.c, pr - po, pq - po, g1, g2, E);
-      pp += g1; np += g2; sp -= (g1 + g2);
-      if (W) { vir_add(W, pr, g1); vir_add(W, pq, g2); vir_add(W, po, -(g1 + g2)); }
+  if constexpr (EXT) {
+    if (f & F_JUNC) {   // evaluated by junction_pass
+      junction_copy(a, sm.cs, sm.cn, sm.cp, o);
+      return;
     }
   }
-  sm.cs[0 * RING + ri] = sb.x; sm.cs[1 * RING + ri] = sb.y; sm.cs[2 * RING + ri] = sb.z;
-  sm.cs[3 * RING + ri] = sp.x; sm.cs[4 * RING + ri] = sp.y; sm.cs[5 * RING + ri] = sp.z;
-  sm.cn[0 * RING + ri] = nb.x; sm.cn[1 * RING + ri] = nb.y; sm.cn[2 * RING + ri] = nb.z;
-  sm.cn[3 * RING + ri] = np.x; sm.cn[4 * RING + ri] = np.y; sm.cn[5 * RING + ri] = np.z;
-  sm.cp[0 * RING + ri] = pp.x; sm.cp[1 * RING + ri] = pp.y; sm.cp[2 * RING + ri] = pp.z;
+  OwnerOut<Real> out{{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  if (f & F_NEXT) owner_eval<Real, EXT>(a, RingSrc<Real>{sm.pos, sm.flg}, o, f, persist, fl, E, W, out);
+  store_owner(sm, ri, out);
 }
 
 // MODE_ENERGY: per-term energies and virial of one owner or nucleotide, added
@@ -167,18 +298,20 @@ __device__ __forceinline__ void stage_slot(const KArgs<Real>& a, const SegSmem<R
   }
 }
 
-// Owner o's terms; MODE_ENERGY adds them to its molecule when `count`.
-template <class Real, int MODE>
-__device__ __forceinline__ void owner_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t o, bool count,
-                                           unsigned& fl) {
+// Owner o's terms.  `home`: o's slot belongs to this strip (the strip before
+// it evaluates o again for its last nucleotides); MODE_ENERGY then adds the
+// energies to the molecule, MODE_STEP records removed terms (rule 2).
+template <class Real, int MODE, bool EXT>
+__device__ __forceinline__ void owner_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t o, int cur,
+                                           bool home, unsigned& fl) {
   if constexpr (MODE == MODE_ENERGY) {
     Real E[NTERMS], W[6];
     for (int k = 0; k < NTERMS; ++k) E[k] = 0;
     for (int k = 0; k < 6; ++k) W[k] = 0;
-    owner_terms(a, sm, o, fl, count ? E : nullptr, count ? W : nullptr);
-    if (count) flush_energy(a, sm.flg[ring(o)] >> 8, E, W);
+    owner_terms<Real, EXT>(a, sm, o, cur, false, fl, home ? E : nullptr, home ? W : nullptr);
+    if (home) flush_energy(a, sm.flg[ring(o)] >> MOL_SHIFT, E, W);
   } else {
-    owner_terms<Real>(a, sm, o, fl, nullptr, nullptr);
+    owner_terms<Real, EXT>(a, sm, o, cur, MODE == MODE_STEP && home, fl, nullptr, nullptr);
   }
 }
 
@@ -218,6 +351,8 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
     V3<Real> Fb{sm.cs[0 * RING + ri], sm.cs[1 * RING + ri], sm.cs[2 * RING + ri]};
     V3<Real> Fp{sm.cs[3 * RING + ri], sm.cs[4 * RING + ri], sm.cs[5 * RING + ri]};
     const int dir = (g & 1) ? -2 : 2;
+    // (a neighbour across a ring's junction has its flag cleared here: its
+    // owner's forces arrive through cs, see owner_terms)
     if (f & F_PREV) {
       const int op = ring(g - dir);
       Fb += V3<Real>{sm.cn[0 * RING + op], sm.cn[1 * RING + op], sm.cn[2 * RING + op]};
@@ -295,7 +430,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
     // applied load on the last base pair (Sec. 4.1, 4.2): f/2 at each centre,
     // torque as a couple normal to its axis; half on each site
     if (f & F_TOP) {
-      const int mol = f >> 8;
+      const int mol = f >> MOL_SHIFT;
       const double* ex = a.ext + 8 * mol;
       V3<Real> Fe{(Real)(0.5 * ex[0]), (Real)(0.5 * ex[1]), (Real)(0.5 * ex[2])};
       const V3<Real> Tq{(Real)ex[3], (Real)ex[4], (Real)ex[5]};
@@ -317,7 +452,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       // rigid body (Sec. 2): force and torque about the centre
       const V3<Real> F = Fb + Fp;
       const V3<Real> Tc = h * cross(um, Fp - Fb);
-      const int mol = f >> 8;
+      const int mol = f >> MOL_SHIFT;
       const uint32_t local = (uint32_t)(g - 2 * a.mol_off[mol]);
       double Xd[3], Vd[3];
       if constexpr (sizeof(Real) == 4) {
@@ -397,7 +532,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       }
     }
   }
-  if constexpr (MODE == MODE_ENERGY) flush_energy(a, sm.flg[ring(g)] >> 8, Eb, Wb);
+  if constexpr (MODE == MODE_ENERGY) flush_energy(a, sm.flg[ring(g)] >> MOL_SHIFT, Eb, Wb);
 }
 
 // One warp's strip: tiles [t0, t1) of SEG slots.  The prologue stages slots
@@ -407,7 +542,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
 // slots B-2 .. B+37) and finishes nucleotides B .. B+31, whose terms come
 // from owners B-2 .. B+33.  An owner's energy is counted by the strip that
 // holds its slot.
-template <class Real, int MODE>
+template <class Real, int MODE, bool EXT>
 __device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t t0, int64_t t1, int cur,
                            int64_t step, unsigned& fl) {
   if (t0 >= t1) return;
@@ -416,21 +551,21 @@ __device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_
   const int64_t s1 = t1 * SEG < a.n ? t1 * SEG : a.n;
   if (lane < 16) stage_slot(a, sm, cur, s0 - 8 + lane);
   __syncwarp();
-  if (a.bubble) {
+  if (EXT && a.bubble) {
     if (lane < 16 && !(lane & 1)) mark_open(a, sm, s0 - 8 + lane);
     __syncwarp();
   }
-  if (lane < 4) owner_pass<Real, MODE>(a, sm, s0 - 2 + lane, lane >= 2 && s0 - 2 + lane < s1, fl);
+  if (lane < 4) owner_pass<Real, MODE, EXT>(a, sm, s0 - 2 + lane, cur, lane >= 2 && s0 - 2 + lane < s1, fl);
   for (int64_t t = t0; t < t1; ++t) {
     const int64_t B = t * SEG;
     __syncwarp();
     stage_slot(a, sm, cur, B + 8 + lane);
     __syncwarp();
-    if (a.bubble) {
+    if (EXT && a.bubble) {
       if (!(lane & 1)) mark_open(a, sm, B + 8 + lane);
       __syncwarp();
     }
-    owner_pass<Real, MODE>(a, sm, B + 2 + lane, B + 2 + lane < s1, fl);
+    owner_pass<Real, MODE, EXT>(a, sm, B + 2 + lane, cur, B + 2 + lane < s1, fl);
     __syncwarp();
     if (B + lane < s1) nucleotide_pass<Real, MODE>(a, sm, B + lane, cur, step, fl);
   }
@@ -442,8 +577,11 @@ __device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_
 // null: nsteps), one bounded grid barrier per step; stop early when a bead
 // moved more than skin/2 (the rebuild kernels run next) or on an error.
 // MODE_FORCES / MODE_ENERGY: one pass with the current list.
-template <class Real, int MODE, int CAPMAX>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 1) engine_kernel(const KArgs<Real> a) {
+// EXT: the instance for systems with circular molecules or the bubble rule
+// (junction pass, open-pair marks, removed terms); the other instance
+// compiles none of it.
+template <class Real, int MODE, int CAPMAX, bool EXT>
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 1) engine_kernel(const __grid_constant__ KArgs<Real> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned s_word;
   __shared__ unsigned s_fl;
@@ -460,9 +598,13 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 1) engine_kernel(
     if (threadIdx.x == 0) s_fl = 0;
     __syncthreads();
     unsigned fl = 0;
+    if (EXT && a.n_junc) {   // circular molecules: junction owners first, then a grid barrier
+      const unsigned r = grid_sync(a.bar, gridDim.x, junction_pass<Real, MODE>(a, cur), a.spin_budget, &s_word);
+      if (r & B_ERRMASK) { errbits = r; break; }
+    }
     const int64_t wpb = blockDim.x >> 5;
     const int64_t nw = gridDim.x * wpb, w = blockIdx.x * wpb + (threadIdx.x >> 5);
-    strip_pass<Real, MODE>(a, sm, w * a.nseg / nw, (w + 1) * a.nseg / nw, cur, step, fl);
+    strip_pass<Real, MODE, EXT>(a, sm, w * a.nseg / nw, (w + 1) * a.nseg / nw, cur, step, fl);
     if (fl) atomicOr(&s_fl, fl);
     __syncthreads();
     if (MODE != MODE_STEP) {

@@ -10,12 +10,17 @@ namespace dsdna {
 
 constexpr int CAPMAX = 64;
 
+// mode | MODE_EXT selects the instance with circular molecules and the bubble rule.
 template <class Real>
 static const void* engine_fn(int mode) {
-  switch (mode) {
-    case MODE_STEP: return (const void*)engine_kernel<Real, MODE_STEP, CAPMAX>;
-    case MODE_FORCES: return (const void*)engine_kernel<Real, MODE_FORCES, CAPMAX>;
-    default: return (const void*)engine_kernel<Real, MODE_ENERGY, CAPMAX>;
+  const bool ext = (mode & MODE_EXT) != 0;
+  switch (mode & ~MODE_EXT) {
+    case MODE_STEP: return ext ? (const void*)engine_kernel<Real, MODE_STEP, CAPMAX, true>
+                               : (const void*)engine_kernel<Real, MODE_STEP, CAPMAX, false>;
+    case MODE_FORCES: return ext ? (const void*)engine_kernel<Real, MODE_FORCES, CAPMAX, true>
+                                 : (const void*)engine_kernel<Real, MODE_FORCES, CAPMAX, false>;
+    default: return ext ? (const void*)engine_kernel<Real, MODE_ENERGY, CAPMAX, true>
+                        : (const void*)engine_kernel<Real, MODE_ENERGY, CAPMAX, false>;
   }
 }
 
@@ -42,10 +47,17 @@ cudaError_t engine_launch(int mode, const KArgs<Real>& a, int grid, int T, size_
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  switch (mode) {
-    case MODE_STEP: return cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_STEP, CAPMAX>, a);
-    case MODE_FORCES: return cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_FORCES, CAPMAX>, a);
-    default: return cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_ENERGY, CAPMAX>, a);
+  const bool ext = (mode & MODE_EXT) != 0;
+  switch (mode & ~MODE_EXT) {
+    case MODE_STEP:
+      return ext ? cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_STEP, CAPMAX, true>, a)
+                 : cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_STEP, CAPMAX, false>, a);
+    case MODE_FORCES:
+      return ext ? cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_FORCES, CAPMAX, true>, a)
+                 : cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_FORCES, CAPMAX, false>, a);
+    default:
+      return ext ? cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_ENERGY, CAPMAX, true>, a)
+                 : cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_ENERGY, CAPMAX, false>, a);
   }
 }
 

@@ -130,7 +130,7 @@ __global__ void k_noalloc_prep(const double* X, const double* u, int64_t n, int6
   if (q % 3 == steric_phase) f |= F_STERIC;
   if (q > 0) f |= F_PREV;
   if (q < N - 1) f |= F_NEXT;
-  topo[g] = f | (m << 8);
+  topo[g] = f | (m << MOL_SHIFT);
   const double x0 = X[3 * g], x1 = X[3 * g + 1], x2 = X[3 * g + 2];
   Xs[g] = x0; Xs[ns + g] = x1; Xs[2 * ns + g] = x2;
   Kw[g] = make_int4(fix32(x0), fix32(x1), fix32(x2), 0);
@@ -205,7 +205,8 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   fill_coef_mixed(*p, a.c);
   a.n = n; a.ns = NA_MAX_NT; a.n_mol = n_mol; a.nseg = (n + 31) / 32; a.cap = NA_CAP;
   a.nsteps = 0; a.noise_mode = 0; a.seed_lo = 0; a.seed_hi = 0;
-  a.bubble = p->bubble_rule ? 1 : 0;
+  a.bubble = p->bubble_rule ? 1 : 0;   // one evaluation without history: rule 2 removes what rule 1 does
+  a.n_junc = 0; a.jslot = nullptr; a.jidx = nullptr; a.jout = nullptr;   // linear molecules only
   a.spin_budget = 4000000000ull;
   a.X = reinterpret_cast<double*>(b + O_X);
   a.V = nullptr; a.Om = nullptr;
@@ -253,13 +254,14 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   if (e == cudaSuccess) e = cudaMemsetAsync(a.ncnt, 0, sizeof(int) * n, st);
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
   k_noalloc_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, u, n, NA_MAX_NT, n_mol, a.mol_off, p->steric_phase, a.X, a.Kw, a.U,
-                                                               const_cast<int*>(a.topo), ctrl);
+                                                               a.topo, ctrl);
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(s->grid, (n + NA_T - 1) / NA_T));
   const int scan_grid = (int)std::min<int64_t>(NA_MAX_GRID, std::max<int64_t>(1, ((int64_t)H + 2047) / 2048));
   e = rebuild_launch<float>(a, scan_grid, st);
-  if (e == cudaSuccess) e = engine_launch<float>(MODE_FORCES, a, grid, NA_T, s->smem, st);
+  // the bubble rule runs in the kernel instance that has it (same launch bounds, so the same grid fits)
+  if (e == cudaSuccess) e = engine_launch<float>(MODE_FORCES | (a.bubble ? MODE_EXT : 0), a, grid, NA_T, s->smem, st);
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
   k_noalloc_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.fout, n, F_bead, F_patch);
   e = cudaGetLastError();

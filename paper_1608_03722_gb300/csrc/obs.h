@@ -12,6 +12,7 @@ struct ObsArgs {
   int64_t n;          // row stride of the [3][n] arrays (nucleotides rounded up to 32)
   int64_t g0;         // first slot of the molecule
   int N;              // base pairs of the molecule
+  int ring;           // 1: circular molecule (closed strands, no closure path)
   double h;           // ell / 2
   double rc2;         // hydrogen-bond break distance squared
   double* mid;        // [3*N] scratch

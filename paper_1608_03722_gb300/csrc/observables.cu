@@ -67,23 +67,24 @@ __global__ void obs_bp_kernel(ObsArgs a) {
 __device__ __forceinline__ D3 ld3(const double* p, int k) { return d3(p[3 * k], p[3 * k + 1], p[3 * k + 2]); }
 
 // frame (f, v, t) of base-pair step k: t along the axis, f the bead-bead
-// vector of base pair k projected normal to t
+// vector of base pair k projected normal to t (on a ring step N - 1 closes it)
 __device__ __forceinline__ void frame(const ObsArgs& a, int k, D3* f, D3* v, D3* t) {
-  *t = unit(sub(ld3(a.mid, k + 1), ld3(a.mid, k)));
+  *t = unit(sub(ld3(a.mid, (k + 1) % a.N), ld3(a.mid, k)));
   D3 w = sub(ld3(a.cb, k), ld3(a.ca, k));
   w = sub(w, scl(dt3(w, *t), *t));
   *f = unit(w);
   *v = cr3(*t, *f);
 }
 
-// twist increment alpha + gamma between frames k and k+1 (ZYZ Euler angles)
+// twist increment alpha + gamma between frames k and k+1 (ZYZ Euler angles):
+// N - 2 increments on a linear molecule, N on a ring
 __global__ void obs_twist_kernel(ObsArgs a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   double inc = 0.0;
-  if (k + 2 < a.N) {
+  if (a.ring ? k < a.N : k + 2 < a.N) {
     D3 f0, v0, t0, f1, v1, t1;
     frame(a, k, &f0, &v0, &t0);
-    frame(a, k + 1, &f1, &v1, &t1);
+    frame(a, (k + 1) % a.N, &f1, &v1, &t1);
     // R_ij = e_i(k) . e_j(k+1) with e = (f, v, t)
     const double R11 = dt3(f0, f1), R12 = dt3(f0, v1), R21 = dt3(v0, f1), R22 = dt3(v0, v1);
     inc = atan2(R21 - R12, R11 + R22);
@@ -140,11 +141,12 @@ __device__ __forceinline__ double seg_lk(D3 r1, D3 r2, D3 r3, D3 r4) {
   return sg > 0.0 ? om : (sg < 0.0 ? -om : 0.0);
 }
 
-// Gauss double sum over all segment pairs of the closed curves; curve B is
-// staged through shared memory in tiles
+// Gauss double sum over all segment pairs of the closed curves (the bead
+// curves of a ring are closed already; a linear molecule's carry the four
+// closure points); curve B is staged through shared memory in tiles
 __global__ void obs_lk_kernel(ObsArgs a) {
   __shared__ double tb[2 * 128 * 3];
-  const int M = a.N + 4;
+  const int M = a.ring ? a.N : a.N + 4;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   D3 r1 = d3(0, 0, 0), r2 = d3(0, 0, 0);
   if (i < M) { r1 = ld3(a.ca, i); r2 = ld3(a.ca, (i + 1) % M); }
@@ -176,8 +178,8 @@ cudaError_t obs_launch(const ObsArgs& a, unsigned flags, cudaStream_t st) {
   obs_bp_kernel<<<nb, T, 0, st>>>(a);
   if (a.N >= 2) obs_twist_kernel<<<nb, T, 0, st>>>(a);
   if ((flags & 8u) && a.N >= 2) {
-    obs_close_kernel<<<1, 256, 0, st>>>(a);
-    const int M = a.N + 4;
+    if (!a.ring) obs_close_kernel<<<1, 256, 0, st>>>(a);
+    const int M = a.ring ? a.N : a.N + 4;
     obs_lk_kernel<<<(M + 127) / 128, 128, 0, st>>>(a);
   }
   return cudaGetLastError();

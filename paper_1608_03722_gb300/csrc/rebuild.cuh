@@ -96,7 +96,7 @@ __device__ void rebuild_bin(const KArgs<Real>& a, int cur, unsigned& fl) {
       }
     }
     const int packed = (w[0] & 0x3ff) | ((w[1] & 0x3ff) << 10) | ((w[2] & 0x3ff) << 20);
-    const int mol = a.topo[g] >> 8;
+    const int mol = a.topo[g] >> MOL_SHIFT;
     const unsigned k = cell_key(a, mol, ci[0], ci[1], ci[2]);
     a.key[g] = (int)k;
     a.wpos[g] = make_float4(pw[0], pw[1], pw[2], __int_as_float(mol));

@@ -38,10 +38,10 @@ class dsdna_params(C.Structure):
 class dsdna_system(C.Structure):
     _fields_ = [("n_mol", C.c_int), ("n_bp", C.POINTER(C.c_int)), ("X", C.POINTER(C.c_double)),
                 ("V", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double)), ("Om", C.POINTER(C.c_double)),
-                ("tether", C.POINTER(C.c_int)), ("gc", C.POINTER(C.c_byte))]
+                ("tether", C.POINTER(C.c_int)), ("gc", C.POINTER(C.c_byte)), ("circular", C.POINTER(C.c_int))]
 
 
-def _system(n_bp, X, V, u, Om, tether, gc):
+def _system(n_bp, X, V, u, Om, tether, gc, circular=None):
     """dsdna_system for the given arrays; returns (struct, arrays to keep alive)."""
     nb = np.ascontiguousarray(np.atleast_1d(n_bp), dtype=np.int32)
     n = 2 * int(nb.sum())
@@ -50,10 +50,14 @@ def _system(n_bp, X, V, u, Om, tether, gc):
     gg = None if gc is None else np.ascontiguousarray(np.asarray(gc) != 0, dtype=np.int8)
     if gg is not None and gg.size != n // 2:
         raise ValueError(f"gc needs one flag per base pair ({n // 2}), got {gg.size}")
+    cc = None if circular is None else np.ascontiguousarray(np.atleast_1d(circular), dtype=np.int32)
+    if cc is not None and cc.size != nb.size:
+        raise ValueError(f"circular needs one flag per molecule ({nb.size}), got {cc.size}")
     sys = dsdna_system(len(nb), nb.ctypes.data_as(C.POINTER(C.c_int)), _dp(X), _dp(V), _dp(u), _dp(Om),
                        None if tt is None else tt.ctypes.data_as(C.POINTER(C.c_int)),
-                       None if gg is None else gg.ctypes.data_as(C.POINTER(C.c_byte)))
-    return sys, (nb, X, V, u, Om, tt, gg)
+                       None if gg is None else gg.ctypes.data_as(C.POINTER(C.c_byte)),
+                       None if cc is None else cc.ctypes.data_as(C.POINTER(C.c_int)))
+    return sys, (nb, X, V, u, Om, tt, gg, cc)
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -112,6 +116,8 @@ def load(build_if_missing: bool = True):
     L.dsdna_get_state.argtypes = [C.c_void_p, C.c_int, d, d, d, d]
     L.dsdna_set_state.argtypes = [C.c_void_p, C.c_int, d, d, d, d]
     L.dsdna_compute_forces.argtypes = [C.c_void_p, d, d]
+    L.dsdna_get_bubble_mask.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+    L.dsdna_set_bubble_mask.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
     L.dsdna_neighbor_pairs.argtypes = [C.c_void_p, C.c_int64, P(C.c_int64), P(C.c_int64), P(C.c_int64)]
     L.dsdna_get_info.argtypes = [C.c_void_p, P(dsdna_info)]
     L.dsdna_step_counter.argtypes = [C.c_void_p]
@@ -204,11 +210,12 @@ class _TorchAllocator:
 
 
 def dsdna_create(params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, tether=None, stream=None,
-                 allocator="torch", gc=None):
+                 allocator="torch", gc=None, circular=None):
     """Create a context; returns (handle, keepalive).  X/u and V/Om are (n_nt, 3) arrays or None;
-    gc is one flag per base pair (1 = G.C, hydrogen-bond stiffness K2_gc) or None."""
+    gc is one flag per base pair (1 = G.C, hydrogen-bond stiffness K2_gc) or None; circular one
+    flag per molecule (1 = ring) or None."""
     L = load()
-    sys, _keep = _system(n_bp, X, V, u, Om, tether, gc)
+    sys, _keep = _system(n_bp, X, V, u, Om, tether, gc, circular)
     alloc = None
     if stream is None:
         import torch
@@ -223,10 +230,10 @@ def dsdna_create(params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, te
 
 
 def dsdna_autotune(params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, tether=None, trial_steps=50,
-                   stream=None, allocator="torch", gc=None):
+                   stream=None, allocator="torch", gc=None, circular=None):
     """Fastest (skin, CTA size, CTAs per SM) for this system; returns (params, ns per nucleotide-step)."""
     L = load()
-    sys, _keep = _system(n_bp, X, V, u, Om, tether, gc)
+    sys, _keep = _system(n_bp, X, V, u, Om, tether, gc, circular)
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
@@ -243,13 +250,13 @@ class Context:
     """One engine context on the current CUDA device and stream."""
 
     def __init__(self, params: dsdna_params, n_bp, X=None, V=None, u=None, Om=None, tether=None, stream=None,
-                 allocator="torch", gc=None):
+                 allocator="torch", gc=None, circular=None):
         self.lib = load()
         self.params = params
         self.n_bp = np.ascontiguousarray(np.atleast_1d(n_bp), dtype=np.int32)
         self.n_nt = 2 * int(self.n_bp.sum())
         self.off = np.concatenate([[0], np.cumsum(self.n_bp)]).astype(np.int64)
-        self.h, self._alloc = dsdna_create(params, self.n_bp, X, V, u, Om, tether, stream, allocator, gc)
+        self.h, self._alloc = dsdna_create(params, self.n_bp, X, V, u, Om, tether, stream, allocator, gc, circular)
 
     def _mol_len(self, mol):
         return self.n_nt if mol < 0 else 2 * int(self.n_bp[mol])
@@ -291,6 +298,18 @@ class Context:
         n = self._mol_len(mol)
         arrs = [_f64(a, n) for a in (X, V, u, Om)]
         _check(self.h, self.lib.dsdna_set_state(self.h, int(mol), *[_dp(a) for a in arrs]))
+
+    def get_bubble_mask(self, mol=-1):
+        """dsdna_get_bubble_mask: uint8 per nucleotide (bit 0 dihedral, bit 1 bending removed)."""
+        m = np.zeros(self._mol_len(mol), np.uint8)
+        _check(self.h, self.lib.dsdna_get_bubble_mask(self.h, int(mol), m.ctypes.data_as(C.c_void_p)))
+        return m
+
+    def set_bubble_mask(self, mask, mol=-1):
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        if m is not None and m.size != self._mol_len(mol):
+            raise ValueError("bubble mask needs one byte per nucleotide")
+        _check(self.h, self.lib.dsdna_set_bubble_mask(self.h, int(mol), None if m is None else m.ctypes.data_as(C.c_void_p)))
 
     def compute_forces(self):
         Fb = np.zeros((self.n_nt, 3)); Fp = np.zeros((self.n_nt, 3))

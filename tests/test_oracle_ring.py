@@ -154,3 +154,21 @@ def test_linking_number_is_conserved_by_langevin_dynamics():
     assert abs(ob["lk"] - 5) < 1e-6, ob
     assert abs(ob["tw"] + ob["wr"] - ob["lk"]) < 1e-9
     assert abs(ob["tw"] - tw0) > 1e-3      # the state moved
+
+
+@pytest.mark.parametrize("N", [30, 31, 32, 33, 34, 35])
+@pytest.mark.parametrize("phase", [0, 1, 2])
+def test_ring_steric_beads_stay_three_apart(N, phase):
+    """Sec. 2 steric typing on a ring: along each strand consecutive steric
+    beads are 3 nucleotides apart, except one gap of 4 or 5 when N is not a
+    multiple of 3 (read from the typed pair set: two beads of one strand
+    interact only if both are steric)."""
+    X, u = I.ring_helix(N, N // 10)
+    p = O.params(ring=[1], steric_phase=phase)
+    prs = O.pairs(p, N, X, u, extra=1e3)
+    for s in (0, 1):
+        st = sorted({int(g) for pr in prs if (pr[0] & 1) == s and (pr[1] & 1) == s for g in pr})
+        q = np.sort([(g // 2) if s == 0 else N - 1 - g // 2 for g in st])
+        gaps = np.diff(np.concatenate([q, [q[0] + N]]))
+        assert gaps.min() >= 3 and (gaps > 3).sum() == (0 if N % 3 == 0 else 1), (s, gaps)
+        assert q[0] == phase      # the pattern starts at the 5' end as on a linear strand
