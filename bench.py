@@ -76,7 +76,7 @@ def build_workload(name: str, seed: int = 0, n_bp: int = 1_000_000):
 # kernel from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
 # one-step launches on the 500 kbp confined workload), keyed by a hash of the
 # kernel sources it was taken on: a changed kernel reports no traffic.
-ENGINE_TRAFFIC = {"1ce3e28fc4064ff8": 192.8}   # 1 Mbp confined workload, skin 0.3
+ENGINE_TRAFFIC = {"e7cb2222ada9caed": 192.8}   # 1 Mbp confined workload, skin 0.3
 ENGINE_SOURCES = ("engine.cuh", "engine_kernels.cuh", "kern_mixed.cu")   # the step kernel's code
 
 
@@ -264,6 +264,36 @@ def compare_paper(D, torch, steps=100, reps=5):
     return out
 
 
+def compare_ring(D, torch, n_bp=500, lk=47, samples=(0, 50_000, 100_000, 200_000, 400_000), n_batch=64,
+                 steps=1000, reps=3):
+    """Sec. 6 / Fig. 10: a 500 bp ring wound 47 turns instead of 50 (Delta Lk
+    = -3, sigma = -0.06).  Twist, writhe and linking number along one
+    trajectory (Lk must stay 47 while twist turns into writhe), and the step
+    rate of one ring and of a batch of rings (the ring kernel instance with its
+    junction pass)."""
+    from paper_1608_03722_gb300 import inputs as I
+    X, u = I.ring_helix(n_bp, lk)
+    ctx = D.Context(D.dsdna_default_params(seed=1), [n_bp], X=X, u=u, circular=[1])
+    traj, done = [], 0
+    for s in samples:
+        ctx.step(s - done)
+        done = s
+        o = ctx.observables(0, flags=D.OBS_TW | D.OBS_LK)
+        traj.append({"step": s, "tw": o["tw"], "wr": o["wr"], "lk": o["lk"]})
+    t1 = timed_steps(ctx, torch, steps, reps)
+    ctx.close()
+    Xs = np.concatenate([I.ring_helix(n_bp, lk, center=(40.0 * (m % 8), 40.0 * (m // 8), 0.0))[0] for m in range(n_batch)])
+    us = np.concatenate([u] * n_batch)
+    ctx = D.Context(D.dsdna_default_params(seed=2), [n_bp] * n_batch, X=Xs, u=us, circular=[1] * n_batch)
+    tb = timed_steps(ctx, torch, steps, reps)
+    ctx.close()
+    return {"workload": f"{n_bp} bp ring, Lk {lk} (Delta Lk = {lk - n_bp // 10}), Langevin kT=1, dt=0.005",
+            "trajectory": traj,
+            "one_ring_steps_per_s": steps * reps / t1,
+            "batch": {"rings": n_batch, "value": 2 * n_bp * n_batch * steps * reps / tb, "unit": UNIT,
+                      "steps_per_s": steps * reps / tb}}
+
+
 def reference_arm(args, ws, rank):
     if rank != 0:
         return 0
@@ -438,6 +468,7 @@ def main():
     if rank == 0 and not args.no_compare:
         compare = compare_batched(D, torch)
         compare["paper_benchmark"] = compare_paper(D, torch)
+        compare["supercoiled_ring"] = compare_ring(D, torch)
         from paper_1608_03722_gb300 import surrogate as SUR
         st = SUR.run_sweep_study(n_train=256, n_test=64, n_query=32, length=(100, 400), steps=8000,
                                  measure_from=2000, every=100, iters=3000)
