@@ -237,6 +237,15 @@ int dsdna_energy_virial(dsdna_ctx* ctx, int mol, double energy[DSDNA_NTERMS], do
  * reductions on the device.  DSDNA_OBS_LK costs O(N^2) in the molecule length. */
 int dsdna_observables(dsdna_ctx* ctx, int mol, unsigned flags, dsdna_obs* out);
 
+/* Per-molecule profiles behind dsdna_observables, for the persistence-length
+ * and torsional-persistence correlators of Sec. 3.1-3.2: centre[3*N] the
+ * base-pair centres (midpoint of the two patches, the centreline whose
+ * tangents Sec. 3.1 correlates), twist[N-2] (a ring: [N]) the twist
+ * increment of each pair of consecutive base-pair-step frames in turns
+ * (App. B, alpha + gamma / 2 pi).  Caller-owned host arrays, either may be
+ * NULL.  Synchronises. */
+int dsdna_profiles(dsdna_ctx* ctx, int mol, double* centre, double* twist);
+
 /* Copy the state of molecule mol (-1: all) to caller-owned host arrays
  * [3*n] each (any may be NULL).  Synchronises.  Also allowed on a poisoned
  * context (post-mortem: the state at the step that raised the error). */

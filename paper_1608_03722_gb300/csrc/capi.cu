@@ -491,7 +491,7 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   ALLOC(nrebuild, unsigned long long, 1);
   ALLOC(fout, double, 6 * nn); ALLOC(eout, double, (size_t)c->n_mol * EOUT_STRIDE);
   ALLOC(stage, double, 12 * nn);
-  ALLOC(obs_scratch, double, 3 * (size_t)(3 * (c->maxN + 4)));
+  ALLOC(obs_scratch, double, 3 * (size_t)(3 * (c->maxN + 4)) + (size_t)c->maxN + 4);   // curves + twist increments
   ALLOC(obs_out, double, 8);
   ALLOC(steps_left, int64_t, 1);
   ALLOC(iters, unsigned, 4);
@@ -917,6 +917,40 @@ extern "C" int dsdna_observables(dsdna_ctx* c, int mol, unsigned flags, dsdna_ob
   out->tw_ideal = a.N >= 3 ? (double)ninc * (c->p.d_dih + M_PI) / (2.0 * M_PI) : 0.0;
   out->lk = (flags & DSDNA_OBS_LK) ? o[4] : 0.0;
   out->wr = (flags & DSDNA_OBS_LK) ? o[4] - o[2] : 0.0;
+  return DSDNA_OK;
+}
+
+// Per-base-pair centreline (patch midpoints, Sec. 3.1) and per-step twist
+// increments (App. B) of one molecule, from the same device reductions as
+// dsdna_observables; the FP64 arrays go to caller-owned host memory.
+extern "C" int dsdna_profiles(dsdna_ctx* c, int mol, double* centre, double* twist) {
+  if (!c) return DSDNA_EINVAL;
+  if (c->poisoned) return fail(c, DSDNA_ESTATE, "context poisoned by an earlier error");
+  if (mol < 0 || mol >= c->n_mol) return fail(c, DSDNA_EINVAL, "molecule index out of range");
+  int rc = sync_check(c);
+  if (rc) return rc;
+  const int N = c->n_bp[mol];
+  const int ninc = c->circular[mol] ? N : std::max(0, N - 2);
+  const int cur = (int)(c->step & 1);
+  ObsArgs a{};
+  a.n = c->ns;
+  a.X = c->fp64() ? c->X + (size_t)cur * 3 * c->ns : c->X;
+  a.uf = c->fp64() ? nullptr : c->U + (size_t)cur * c->ns;
+  a.ud = c->fp64() ? c->ud + (size_t)cur * 3 * c->ns : nullptr;
+  a.g0 = 2 * c->off[mol];
+  a.N = N;
+  a.ring = c->circular[mol];
+  a.h = 0.5 * c->p.ell;
+  a.rc2 = c->p.rc_hb * c->p.rc_hb;
+  a.mid = c->obs_scratch;
+  a.ca = a.mid + 3 * (size_t)(c->maxN + 4);
+  a.cb = a.ca + 3 * (size_t)(c->maxN + 4);
+  a.out = c->obs_out;
+  a.inc = c->obs_scratch + 9 * (size_t)(c->maxN + 4);   // beyond the three curves
+  CK(obs_launch(a, DSDNA_OBS_TW, c->st), "profiles");
+  if (centre) CK(cudaMemcpyAsync(centre, a.mid, sizeof(double) * 3 * (size_t)N, cudaMemcpyDeviceToHost, c->st), "read centre");
+  if (twist && ninc) CK(cudaMemcpyAsync(twist, a.inc, sizeof(double) * (size_t)ninc, cudaMemcpyDeviceToHost, c->st), "read twist");
+  CK(cudaStreamSynchronize(c->st), "profiles sync");
   return DSDNA_OK;
 }
 

@@ -19,6 +19,7 @@ struct ObsArgs {
   double* ca;         // [3*(N+4)] scratch: closed curve of strand A
   double* cb;         // [3*(N+4)] scratch: closed curve of strand B
   double* out;        // [8]: rz, broken count, tw, -, lk
+  double* inc;        // [N-2] (ring: [N]) twist increments in turns, or nullptr
 };
 
 cudaError_t obs_launch(const ObsArgs& a, unsigned flags, cudaStream_t st);

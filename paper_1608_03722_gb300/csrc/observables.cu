@@ -88,6 +88,7 @@ __global__ void obs_twist_kernel(ObsArgs a) {
     // R_ij = e_i(k) . e_j(k+1) with e = (f, v, t)
     const double R11 = dt3(f0, f1), R12 = dt3(f0, v1), R21 = dt3(v0, f1), R22 = dt3(v0, v1);
     inc = atan2(R21 - R12, R11 + R22);
+    if (a.inc) a.inc[k] = inc / (2.0 * 3.14159265358979323846);
   }
   block_add(inc / (2.0 * 3.14159265358979323846), a.out + 2);
   if (k == 0) a.out[0] = a.mid[3 * (a.N - 1) + 2] - a.mid[2];

@@ -87,7 +87,8 @@ class dsdna_prof(C.Structure):
 EXPORTS = ["dsdna_default_params", "dsdna_create", "dsdna_set_external_force_torque", "dsdna_step",
            "dsdna_step_profiled", "dsdna_synchronize", "dsdna_energy_virial", "dsdna_observables", "dsdna_get_state", "dsdna_set_state",
            "dsdna_compute_forces", "dsdna_neighbor_pairs", "dsdna_get_info", "dsdna_step_counter",
-           "dsdna_last_error", "dsdna_destroy", "dsdna_forces_noalloc", "dsdna_autotune"]
+           "dsdna_last_error", "dsdna_destroy", "dsdna_forces_noalloc", "dsdna_autotune", "dsdna_profiles",
+           "dsdna_get_bubble_mask", "dsdna_set_bubble_mask"]
 
 _lib = None
 
@@ -114,6 +115,7 @@ def load(build_if_missing: bool = True):
     L.dsdna_energy_virial.argtypes = [C.c_void_p, C.c_int, d, d]
     L.dsdna_observables.argtypes = [C.c_void_p, C.c_int, C.c_uint, P(dsdna_obs)]
     L.dsdna_get_state.argtypes = [C.c_void_p, C.c_int, d, d, d, d]
+    L.dsdna_profiles.argtypes = [C.c_void_p, C.c_int, d, d]
     L.dsdna_set_state.argtypes = [C.c_void_p, C.c_int, d, d, d, d]
     L.dsdna_compute_forces.argtypes = [C.c_void_p, d, d]
     L.dsdna_get_bubble_mask.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
@@ -256,6 +258,7 @@ class Context:
         self.n_bp = np.ascontiguousarray(np.atleast_1d(n_bp), dtype=np.int32)
         self.n_nt = 2 * int(self.n_bp.sum())
         self.off = np.concatenate([[0], np.cumsum(self.n_bp)]).astype(np.int64)
+        self.circular = np.zeros(len(self.n_bp), np.int32) if circular is None else np.asarray(circular, np.int32)
         self.h, self._alloc = dsdna_create(params, self.n_bp, X, V, u, Om, tether, stream, allocator, gc, circular)
 
     def _mol_len(self, mol):
@@ -286,6 +289,13 @@ class Context:
         o = dsdna_obs()
         _check(self.h, self.lib.dsdna_observables(self.h, int(mol), int(flags), C.byref(o)))
         return dict(rz=o.rz, denat=o.denat, tw=o.tw, tw_ideal=o.tw_ideal, lk=o.lk, wr=o.wr)
+
+    def profiles(self, mol=0):
+        """dsdna_profiles: (centre [N, 3], twist increments [N-2], or [N] on a ring)."""
+        N = int(self.n_bp[mol])
+        cen = np.zeros((N, 3)); tw = np.zeros(N if self.circular[mol] else max(0, N - 2))
+        _check(self.h, self.lib.dsdna_profiles(self.h, int(mol), _dp(cen), _dp(tw)))
+        return cen, tw
 
     def get_state(self, mol=-1, out=None):
         n = self._mol_len(mol)

@@ -92,6 +92,41 @@ def ring_helix(n_bp: int, lk: int, center=(0.0, 0.0, 0.0)):
     return place(axis, d)
 
 
+def wlc_helix(n_bp: int, lp_bp: float, rng: np.random.Generator, origin=(0.0, 0.0, 0.0), clearance: float = 2.5,
+              tries: int = 100):
+    """Relaxed helix (36 degrees per base pair about a parallel-transported
+    frame) along a worm-like axis whose tangents decorrelate as
+    exp(-s / lp_bp) per base pair; axis points more than 10 bp apart along the
+    chain stay at least `clearance` nm apart (redrawn otherwise)."""
+    c = 1.0 - math.exp(-1.0 / lp_bp)
+    for _ in range(tries):
+        t = np.empty((n_bp, 3)); t[0] = (0.0, 0.0, 1.0)
+        for k in range(1, n_bp):
+            a = rng.normal(size=3)
+            a -= a.dot(t[k - 1]) * t[k - 1]
+            a /= np.linalg.norm(a)
+            ct = 1.0 - min(2.0, rng.exponential(c))
+            t[k] = ct * t[k - 1] + math.sqrt(max(0.0, 1.0 - ct * ct)) * a
+            t[k] /= np.linalg.norm(t[k])
+        axis = np.asarray(origin, float)[None, :] + RISE * np.concatenate([[np.zeros(3)], np.cumsum(t[:-1], 0)])
+        far = np.abs(np.arange(n_bp)[:, None] - np.arange(n_bp)[None, :]) > 10
+        dist = np.linalg.norm(axis[:, None, :] - axis[None, :, :], axis=2)
+        if (dist[far] >= clearance).all():
+            break
+    else:
+        raise RuntimeError("no self-avoiding worm-like axis found")
+    n = np.empty((n_bp, 3))
+    ref = np.array([1.0, 0.0, 0.0])
+    n[0] = ref - ref.dot(t[0]) * t[0]; n[0] /= np.linalg.norm(n[0])
+    for k in range(1, n_bp):                  # parallel transport of the normal
+        v = n[k - 1] - n[k - 1].dot(t[k]) * t[k]
+        n[k] = v / np.linalg.norm(v)
+    b = np.cross(t, n)
+    ang = TWIST * np.arange(n_bp)
+    d = np.cos(ang)[:, None] * n + np.sin(ang)[:, None] * b
+    return place(axis, d)
+
+
 def maxwell(u: np.ndarray, rng: np.random.Generator, kT: float = 1.0, mass: float = 1.0, ell: float = ELL,
             frozen: np.ndarray | None = None):
     """Maxwell-Boltzmann centre and angular velocities (angular normal to u)."""

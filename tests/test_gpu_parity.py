@@ -371,3 +371,18 @@ def test_denaturation_rules_match_oracle(prec):
     Eoff = O.forces(O.params(**kw), n_bp, Xs, us)["energy"].sum(axis=0)
     assert Eoff[D.E_DIHEDRAL] - Eo[D.E_DIHEDRAL] > 1e-3 or Eo[D.E_DIHEDRAL] - Eoff[D.E_DIHEDRAL] > 1e-3
     assert abs(Eoff[D.E_HBOND] - Eo[D.E_HBOND]) > 1e-3
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_profiles_sum_to_the_observables(prec):
+    """dsdna_profiles: the twist increments add up to the oracle's twist and the
+    centreline is the patch midpoint of each base pair (Sec. 3.1, App. B)."""
+    cfg = dense_walk(300, seed=11)
+    ctx = ctx_for(cfg, prec)
+    cen, tw = ctx.profiles(0)
+    Xs, _, us, _ = ctx.get_state()
+    ctx.close()
+    oo = O.observables(oparams(cfg), cfg.n_bp, Xs, us, mol=0)
+    assert abs(tw.sum() - oo["tw"]) < 1e-9, (tw.sum(), oo["tw"])
+    p = Xs + 0.25 * us
+    assert np.abs(cen - 0.5 * (p[0::2] + p[1::2])).max() < 1e-6
