@@ -93,21 +93,34 @@ def ring_helix(n_bp: int, lk: int, center=(0.0, 0.0, 0.0)):
 
 
 def wlc_helix(n_bp: int, lp_bp: float, rng: np.random.Generator, origin=(0.0, 0.0, 0.0), clearance: float = 2.5,
-              tries: int = 100):
+              seg: int = 10, tries: int = 100):
     """Relaxed helix (36 degrees per base pair about a parallel-transported
-    frame) along a worm-like axis whose tangents decorrelate as
-    exp(-s / lp_bp) per base pair; axis points more than 10 bp apart along the
-    chain stay at least `clearance` nm apart (redrawn otherwise)."""
-    c = 1.0 - math.exp(-1.0 / lp_bp)
+    frame) along a smooth worm-like axis: tangents drawn every `seg` base
+    pairs with <t . t'> = exp(-seg / lp_bp), interpolated by slerp in between,
+    so the bending is spread over `seg` base pairs as thermal bending of the
+    duplex is.  Axis points more than 10 bp apart along the chain stay at
+    least `clearance` nm apart (redrawn otherwise)."""
+    nc = (n_bp + seg - 1) // seg + 1
+    c = 1.0 - math.exp(-float(seg) / lp_bp)
     for _ in range(tries):
-        t = np.empty((n_bp, 3)); t[0] = (0.0, 0.0, 1.0)
-        for k in range(1, n_bp):
+        T = np.empty((nc, 3)); T[0] = (0.0, 0.0, 1.0)
+        for k in range(1, nc):
             a = rng.normal(size=3)
-            a -= a.dot(t[k - 1]) * t[k - 1]
+            a -= a.dot(T[k - 1]) * T[k - 1]
             a /= np.linalg.norm(a)
-            ct = 1.0 - min(2.0, rng.exponential(c))
-            t[k] = ct * t[k - 1] + math.sqrt(max(0.0, 1.0 - ct * ct)) * a
-            t[k] /= np.linalg.norm(t[k])
+            ct = max(-1.0, 1.0 - rng.exponential(c))
+            T[k] = ct * T[k - 1] + math.sqrt(1.0 - ct * ct) * a
+            T[k] /= np.linalg.norm(T[k])
+        t = np.empty((n_bp, 3))
+        for i in range(n_bp):
+            j, f = divmod(i, seg)
+            f /= seg
+            om = math.acos(max(-1.0, min(1.0, float(T[j].dot(T[j + 1])))))
+            if om < 1e-9:
+                t[i] = T[j]
+            else:
+                t[i] = (math.sin((1.0 - f) * om) * T[j] + math.sin(f * om) * T[j + 1]) / math.sin(om)
+            t[i] /= np.linalg.norm(t[i])
         axis = np.asarray(origin, float)[None, :] + RISE * np.concatenate([[np.zeros(3)], np.cumsum(t[:-1], 0)])
         far = np.abs(np.arange(n_bp)[:, None] - np.arange(n_bp)[None, :]) > 10
         dist = np.linalg.norm(axis[:, None, :] - axis[None, :, :], axis=2)

@@ -89,14 +89,15 @@ class Correlators:
 
 
 def measure(n_mol=512, n_bp=300, equil=1_000_000, every=10_000, samples=100, seed=0, trim=5, groups=8,
-            s_max=120, m_max=150, s_fit=(1, 100), m_fit=(1, 150), precision=None, init_lp=None, log=None):
+            s_max=120, m_max=150, s_fit=(1, 100), m_fit=(1, 150), precision=None, init_lp=None, overrides=None,
+            log=None):
     """Run n_mol independent n_bp chains (one context), equilibrate, then sample
     `samples` times every `every` steps; returns the fitted lengths in bp.
     The chains start straight, or (init_lp) along worm-like axes of that
     persistence length, so that equilibration can be checked from both sides."""
     from . import dsdna as D
     from . import inputs as I
-    p = D.dsdna_default_params(seed=seed)
+    p = D.dsdna_default_params(seed=seed, **(overrides or {}))
     if precision is not None:
         p.precision = precision
     X = u = None
@@ -120,7 +121,8 @@ def measure(n_mol=512, n_bp=300, equil=1_000_000, every=10_000, samples=100, see
     ctx.close()
     out = acc.result(s_fit, m_fit)
     out.update({"n_mol": n_mol, "n_bp": n_bp, "equilibration_steps": equil, "sample_every": every,
-                "samples": samples, "trim_bp": trim, "init_lp_bp": init_lp, "seconds": time.time() - t0,
+                "samples": samples, "trim_bp": trim, "init_lp_bp": init_lp, "overrides": overrides or {},
+                "seconds": time.time() - t0,
                 "seconds_equilibration": t_eq, "paper": {"l_p_bp": "143 +- 7", "l_tau_bp": "512 +- 18"}})
     return out
 
@@ -134,11 +136,14 @@ def main():
     ap.add_argument("--samples", type=int, default=100)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--init-lp", type=float, default=None, help="start along worm-like axes of this l_p (bp)")
+    ap.add_argument("--param", action="append", default=[], metavar="NAME=VALUE",
+                    help="override a model parameter (e.g. K5=400), repeatable")
     ap.add_argument("--out", default=None, help="write the JSON result here")
     a = ap.parse_args()
     import torch
     torch.cuda.init()
-    r = measure(a.n_mol, a.n_bp, a.equil, a.every, a.samples, a.seed, init_lp=a.init_lp)
+    ov = {k: float(v) for k, v in (x.split("=", 1) for x in a.param)}
+    r = measure(a.n_mol, a.n_bp, a.equil, a.every, a.samples, a.seed, init_lp=a.init_lp, overrides=ov)
     short = {k: v for k, v in r.items() if not k.endswith("correlator")}
     print(json.dumps(short))
     if a.out:
