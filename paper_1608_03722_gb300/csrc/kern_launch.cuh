@@ -81,6 +81,11 @@ cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lbps, k_rebuild_list_lanes<Real>, LT, 0);
     const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + LT - 1) / LT, (int64_t)nsm * std::max(1, lbps)));
     k_rebuild_list_lanes<Real><<<lgrid, LT, 0, st>>>(a);
+  } else if (a.table == TABLE_HASH) {
+    // open box: one lane per bead over the row ranges of the hashed blocks
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lbps, k_rebuild_list_lanes_hash<Real>, LT, 0);
+    const int lgrid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + LT - 1) / LT, (int64_t)nsm * std::max(1, lbps)));
+    k_rebuild_list_lanes_hash<Real><<<lgrid, LT, 0, st>>>(a);
   } else {
     // one warp per 32 table entries at a time: enough CTAs for every chunk of
     // a small table, at most a full wave for a large one

@@ -26,16 +26,25 @@ __device__ __forceinline__ unsigned spread3(unsigned v) {   // 10 bits -> every 
   return v;
 }
 
+__device__ __forceinline__ unsigned hash_block(int mol, int bx, int cy, int cz) {
+  unsigned h = (unsigned)bx * 0x8da6b343u ^ (unsigned)cy * 0xd8163841u ^ (unsigned)cz * 0xcb1ab31fu ^
+               (unsigned)mol * 0x9E3779B1u;
+  h ^= h >> 16; h *= 0x7feb352du; h ^= h >> 15; h *= 0x846ca68bu; h ^= h >> 16;
+  return h;
+}
+
 template <class Real>
 __device__ __forceinline__ unsigned cell_key(const KArgs<Real>& a, int mol, int cx, int cy, int cz) {
   if (a.table == TABLE_LINEAR) return (unsigned)cx + (unsigned)a.nc[0] * ((unsigned)cy + (unsigned)a.nc[1] * (unsigned)cz);
   if (a.table == TABLE_MORTON) {   // small periodic box: Morton index of the wrapped cell (no collisions)
     return (spread3((unsigned)cx) | (spread3((unsigned)cy) << 1) | (spread3((unsigned)cz) << 2)) & (a.H - 1u);
   }
-  unsigned h = (unsigned)cx * 0x8da6b343u ^ (unsigned)cy * 0xd8163841u ^ (unsigned)cz * 0xcb1ab31fu ^
-               (unsigned)mol * 0x9E3779B1u;
-  h ^= h >> 16; h *= 0x7feb352du; h ^= h >> 15; h *= 0x846ca68bu; h ^= h >> 16;
-  return h & (a.H - 1u);
+  // open box: (molecule, y, z, x / 8) hashed to a bucket of 8 table entries
+  // holding the 8 x-consecutive cells of that block, so a row of three
+  // x-neighbour cells is one range of the sorted beads (two across a block
+  // edge).  Distinct blocks may share a bucket; the list build skips a range
+  // it has already walked.
+  return (hash_block(mol, cx >> 3, cy, cz) & ((a.H >> 3) - 1u)) << 3 | (unsigned)(cx & 7);
 }
 
 template <class Real>
@@ -625,6 +634,72 @@ __device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl) {
   }
 }
 
+// R4 for the hashed table (open box): one lane per bead in table order.  The
+// 9 rows (dy, dz) of the bead's neighbourhood are each one range of the
+// sorted beads, two where x-1 .. x+1 crosses a block edge.  When two rows of
+// the same bead land in the same bucket (two blocks hashed together) the
+// later row's range is the same range and is skipped, so no pair is listed
+// twice; beads of another block or molecule sharing a bucket fail the
+// distance or molecule test.
+template <class Real>
+__device__ void rebuild_list_lanes_hash(const KArgs<Real>& a, unsigned& fl) {
+  __shared__ int sent[LIST_WARPS][32][LIST_CAP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int JMASK = (1 << NBR_J_BITS) - 1;
+  int* list = sent[w][lane];
+  const unsigned bmask = (a.H >> 3) - 1u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
+    const float4 me = a.cent[t];
+    const int gw = __float_as_int(me.w), g = gw & JMASK;
+    const bool st_g = (gw >> NBR_J_BITS) & 1;
+    const int mol = __float_as_int(a.wpos[g].w);
+    const int cx = (int)floorf(me.x * a.invcellh[0]);
+    const int cy = (int)floorf(me.y * a.invcellh[1]);
+    const int cz = (int)floorf(me.z * a.invcellh[2]);
+    const int lo = cx - 1, hi = cx + 1;
+    const bool split = (lo >> 3) != (hi >> 3);
+    // part 0: cells lo .. (split ? block end : hi) of block lo/8; part 1 (split): cells hi/8*8 .. hi
+    const unsigned a0 = (unsigned)(lo & 7), b0 = split ? 7u : (unsigned)(hi & 7), b1 = (unsigned)(hi & 7);
+    unsigned seen0[9], seen1[9];
+    int cnt = 0, total = 0;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      const int y = cy + r % 3 - 1, z = cz + r / 3 - 1;
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        if (part == 1 && !split) continue;
+        const unsigned b = hash_block(mol, part == 0 ? (lo >> 3) : (hi >> 3), y, z) & bmask;
+        bool dup = false;
+#pragma unroll
+        for (int q = 0; q < r; ++q) dup = dup || (part == 0 ? seen0[q] : seen1[q]) == b;
+        if (part == 0) seen0[r] = b; else seen1[r] = b;
+        if (dup) continue;
+        const unsigned u0 = a.start[(b << 3) | (part == 0 ? a0 : 0u)];
+        const unsigned u1 = a.start[((b << 3) | (part == 0 ? b0 : b1)) + 1u];
+        for (unsigned u = u0; u < u1; ++u) {
+          const float4 o = a.cent[u];
+          const int jw = __float_as_int(o.w), j = jw & JMASK;
+          const float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          const float rl2 = ((g ^ j) & 1) ? a.c.rl_cr2 : ((st_g && ((jw >> NBR_J_BITS) & 1)) ? a.c.rl_ss2 : -1.0f);
+          if (r2 < rl2 && j != g && (a.n_mol == 1 || __float_as_int(a.wpos[j].w) == mol)) {
+            ++total;
+            if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed
+              int q = cnt++;
+              while (q > 0 && (list[q - 1] & ENT_JMASK) > j) { list[q] = list[q - 1]; --q; }
+              list[q] = ent_make(j, 0, 0, 0);
+            }
+          }
+        }
+      }
+    }
+    if (total > a.cap) fl |= B_EOVF;
+    for (int q = 0; q < cnt; ++q) a.nbr[(size_t)q * a.ns + g] = list[q];
+    a.ncnt[g] = cnt;
+  }
+}
+
 // ---------------------------------------------------------------- rebuild kernels
 // The neighbour-list rebuild runs as five ordinary kernels (full occupancy,
 // their own register budgets) between persistent step launches: bin + count,
@@ -651,6 +726,17 @@ template <class Real, int CAPMAX>
 __global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list(const KArgs<Real> a) {
   unsigned fl = 0;
   rebuild_list_warps<Real, CAPMAX>(a, fl);
+  if (fl) atomicOr(a.err, fl & B_ERRMASK);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.rebuild = 0;
+    *a.nrebuild += 1;
+  }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list_lanes_hash(const KArgs<Real> a) {
+  unsigned fl = 0;
+  rebuild_list_lanes_hash<Real>(a, fl);
   if (fl) atomicOr(a.err, fl & B_ERRMASK);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.rebuild = 0;

@@ -386,3 +386,25 @@ def test_profiles_sum_to_the_observables(prec):
     assert abs(tw.sum() - oo["tw"]) < 1e-9, (tw.sum(), oo["tw"])
     p = Xs + 0.25 * us
     assert np.abs(cen - 0.5 * (p[0::2] + p[1::2])).max() < 1e-6
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_open_box_list_with_shared_buckets_equals_brute_force(prec):
+    """Open box: the hashed table puts blocks of 8 x-cells in buckets; four
+    overlapping 400 bp molecules occupy about 500 blocks of 1024 buckets, so
+    two of the 9 rows of a bead share a bucket for a few percent of the 3200
+    beads.  The list holds each pair once and exactly the brute-force set."""
+    rng = np.random.default_rng(3)
+    parts = [I.wlc_helix(400, 50.0, rng) for _ in range(4)]
+    X = np.concatenate([q[0] for q in parts]); u = np.concatenate([q[1] for q in parts])
+    n_bp = [400] * 4
+    ctx = D.Context(D.dsdna_default_params(precision=prec), n_bp, X=X, u=u)
+    pl = ctx.neighbor_pairs()
+    got = {tuple(x) for x in pl}
+    assert len(pl) == len(got), "a pair listed twice"
+    skin = ctx.params.skin + 0.01
+    lo = {tuple(x) for x in O.pairs(O.params(), n_bp, X, u, extra=skin - 1e-4)}
+    hi = {tuple(x) for x in O.pairs(O.params(), n_bp, X, u, extra=skin + 1e-4)}
+    assert lo <= got <= hi and len(lo) > 1000
+    assert ctx.info()["cell_table"] == 8192      # 2^13 entries = 1024 buckets for 3200 beads
+    ctx.close()
