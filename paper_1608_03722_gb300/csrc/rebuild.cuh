@@ -556,9 +556,12 @@ __device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl) {
     const int gw = __float_as_int(me.w), g = gw & JMASK;
     const bool st_g = (gw >> NBR_J_BITS) & 1;
     const int mol = a.n_mol > 1 ? __float_as_int(a.wpos[g].w) : 0;
-    const unsigned key = (unsigned)a.key[g];
-    const int cx = (int)(key % (unsigned)nx), cyz = (int)(key / (unsigned)nx);
-    const int cy = cyz % ny, cz = cyz / ny;
+    // the bead's cell, computed as the binning did from the same wrapped position
+    const int kx = (int)floorf(me.x * a.invcellh[0]), ky = (int)floorf(me.y * a.invcellh[1]),
+              kz = (int)floorf(me.z * a.invcellh[2]);
+    const int cx = kx >= nx ? nx - 1 : (kx < 0 ? 0 : kx);
+    const int cy = ky >= ny ? ny - 1 : (ky < 0 ? 0 : ky);
+    const int cz = kz >= nz ? nz - 1 : (kz < 0 ? 0 : kz);
     // candidate ranges: 9 rows (dy, dz) of three x-consecutive cells, a row
     // that wraps in x split in two; range i holds the cells [k0, k1) and its
     // image as ent_make(0, sx, sy, sz)
