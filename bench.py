@@ -251,7 +251,8 @@ def compare_paper(D, torch, steps=100, reps=5):
     out = {}
     for nx in (10, 40):
         cfg = I.paper_array(nx, nx, 600)
-        p = D.dsdna_default_params(box=cfg.box, skin=0.3)
+        p, _ = D.dsdna_autotune(D.dsdna_default_params(box=cfg.box), cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om,
+                                trial_steps=50)
         ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om)
         t = timed_steps(ctx, torch, steps, reps)
         ctx.close()
@@ -260,6 +261,7 @@ def compare_paper(D, torch, steps=100, reps=5):
         out[key] = {"workload": f"{nx}x{nx} array of 600 bp strands ({cfg.n_nt} nucleotides), periodic box "
                                 f"{cfg.box[0]:.0f}x{cfg.box[1]:.0f}x{cfg.box[2]:.0f} nm",
                     "value": cfg.n_nt * steps_s, "unit": UNIT, "steps_per_s": steps_s,
+                    "autotuned": {"skin": p.skin, "block_threads": p.block_threads, "blocks_per_sm": p.blocks_per_sm},
                     "ms_per_day": steps_s * MS_PER_DAY_PER_STEP_S, "paper": PAPER_FIG11[key]}
     return out
 
