@@ -402,7 +402,8 @@ def main():
     engine_launches = info1["engine_launches"] - info0["engine_launches"]
     # kernels of the timed region: per graph launch one loop-init kernel; per loop
     # iteration one loop-head kernel and one persistent step kernel; five per rebuild
-    gpu_launches = graph_launches + 2 * engine_launches + 5 * rebuilds
+    # unless the step kernel rebuilds the list itself
+    gpu_launches = graph_launches + 2 * engine_launches + (0 if info1["rebuild_in_step"] else 5 * rebuilds)
 
     # Roofline of the dominant kernel: K x S further steps queued launch by launch
     # (dsdna_step_profiled), each step-kernel launch bracketed by CUDA events on

@@ -96,6 +96,9 @@ enum { DSDNA_NOISE_OFF = 0, DSDNA_NOISE_UNIFORM = 1, DSDNA_NOISE_GAUSSIAN = 2 };
 /* Model, integrator and engine parameters.  dsdna_default_params fills the
  * values of Table 1 (force field), Sec. 2 (geometry), App. A (kT = 1,
  * gamma = 1, dt = 0.005 tau_Br, Eq. 16). */
+/* rebuild_mode 0 rebuilds inside the step kernel up to this many nucleotides */
+#define DSDNA_FUSED_REBUILD_MAX_NT 262144
+
 typedef struct dsdna_params {
   double K1, R0, eps_bb, sigma_bb;       /* FENE + backbone WCA */
   double K2, r0_hb, rc_hb;               /* hydrogen bond */
@@ -130,6 +133,11 @@ typedef struct dsdna_params {
    * (<= 0: K2 for every pair). */
   int bubble_rule;                       /* 0 off, 1 while in a bubble, 2 for good */
   double K2_gc;
+  /* Neighbour-list rebuild: 1 separate kernels between step launches, 2
+   * inside the persistent step kernel (grid barriers between its phases; one
+   * launch runs a whole graph chunk of steps), 0 chooses 2 for systems of at
+   * most DSDNA_FUSED_REBUILD_MAX_NT nucleotides without a Morton cell table. */
+  int rebuild_mode;
 } dsdna_params;
 
 /* Molecules and (optional) initial state.  NULL X/u builds ideal relaxed
@@ -186,6 +194,7 @@ typedef struct dsdna_info {
   int64_t cell_table;    /* entries of the cell hash table */
   int64_t device_bytes;  /* bytes allocated on the device */
   int64_t engine_launches; /* persistent step/force/energy kernel launches so far */
+  int rebuild_in_step;   /* 1: the step kernel rebuilds the list itself (rebuild_mode) */
 } dsdna_info;
 
 /* Per-launch timing of dsdna_step_profiled (CUDA events on the context stream). */

@@ -52,8 +52,12 @@ struct dsdna_ctx {
   int4* Kw = nullptr; float4* U = nullptr; double* ud = nullptr;
   int* topo = nullptr; int* img = nullptr; int* kref = nullptr; int* nbr = nullptr; int* ncnt = nullptr;
   int64_t n_junc = 0;            // junction owners of circular molecules (8 per ring)
-  // kernel instance: with circular molecules or the bubble rule, MODE_EXT
-  int kernel_ext() const { return (n_junc > 0 || p.bubble_rule > 0) ? MODE_EXT : 0; }
+  bool fused = false;            // list rebuilt inside the step kernel
+  // kernel instance: with circular molecules or the bubble rule, MODE_EXT;
+  // steps with the rebuild inside, MODE_FUSED
+  int kernel_flags(int mode) const {
+    return ((n_junc > 0 || p.bubble_rule > 0) ? MODE_EXT : 0) | ((fused && mode == MODE_STEP) ? MODE_FUSED : 0);
+  }
   int64_t* jslot = nullptr; int* jidx = nullptr; void* jout = nullptr;
   unsigned* cnt = nullptr; unsigned* start = nullptr; int* key = nullptr;
   float4* cent = nullptr; float4* wpos = nullptr; unsigned* bsum = nullptr;
@@ -349,6 +353,7 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
     return fail(nullptr, DSDNA_EINVAL, "non-positive dt/mass/ell/R0/rc or negative gamma/kT");
   if (p->precision != DSDNA_PREC_MIXED && p->precision != DSDNA_PREC_FP64) return fail(nullptr, DSDNA_EINVAL, "precision");
   if (p->bubble_rule < 0 || p->bubble_rule > 2) return fail(nullptr, DSDNA_EINVAL, "bubble_rule must be 0, 1 or 2");
+  if (p->rebuild_mode < 0 || p->rebuild_mode > 2) return fail(nullptr, DSDNA_EINVAL, "rebuild_mode must be 0, 1 or 2");
   if (p->K2_gc < 0.0) return fail(nullptr, DSDNA_EINVAL, "K2_gc must be >= 0");
   if (p->noise < 0 || p->noise > 2) return fail(nullptr, DSDNA_EINVAL, "noise mode");
   if (p->skin < 0.0 || p->skin > 1.0) return fail(nullptr, DSDNA_EINVAL, "skin must be in [0, 1] nm");
@@ -460,6 +465,9 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
     c->table = TABLE_HASH;
     c->morton_bits = 0;
   }
+  // rebuild inside the step kernel: small systems, linear or hashed table
+  c->fused = c->table != TABLE_MORTON &&
+             (c->p.rebuild_mode == 2 || (c->p.rebuild_mode == 0 && n <= DSDNA_FUSED_REBUILD_MAX_NT));
 
   // allocations
   const bool f64 = c->fp64();
@@ -502,7 +510,7 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
   for (int mode = 0; mode < 3; ++mode) {
     int bps = 0;
-    const int m = mode | c->kernel_ext();
+    const int m = mode | c->kernel_flags(mode);
     cudaError_t e = f64 ? engine_occupancy<double>(m, c->T, &bps, &c->smem[mode])
                         : engine_occupancy<float>(m, c->T, &bps, &c->smem[mode]);
     if (e != cudaSuccess || bps < 1) return bad(fail(c, DSDNA_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e)));
@@ -510,7 +518,8 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
     c->grid[mode] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * nsm, c->nseg));
   }
   c->scan_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 8, ((int64_t)c->H + 2047) / 2048));
-  c->bsum = (unsigned*)dalloc(c, sizeof(unsigned) * (size_t)c->scan_grid);
+  // block sums: one per CTA of the scan kernels, or of the step kernel when it rebuilds
+  c->bsum = (unsigned*)dalloc(c, sizeof(unsigned) * (size_t)std::max(c->scan_grid, c->grid[MODE_STEP]));
   if (!c->bsum) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: bsum"));
 
   // topology flags (Sec. 2; anchored and loaded base pairs of Sec. 4)
@@ -642,11 +651,11 @@ static cudaError_t launch_engine(dsdna_ctx* c, int mode, int64_t nsteps, int64_t
   if (c->fp64()) {
     KArgs<double> a = c->kd;
     a.nsteps = nsteps; a.steps_left = steps_left; a.use_cond = use_cond; a.h_while = hw;
-    return engine_launch<double>(mode | c->kernel_ext(), a, c->grid[mode], c->T, c->smem[mode], c->st);
+    return engine_launch<double>(mode | c->kernel_flags(mode), a, c->grid[mode], c->T, c->smem[mode], c->st);
   }
   KArgs<float> a = c->kf;
   a.nsteps = nsteps; a.steps_left = steps_left; a.use_cond = use_cond; a.h_while = hw;
-  return engine_launch<float>(mode | c->kernel_ext(), a, c->grid[mode], c->T, c->smem[mode], c->st);
+  return engine_launch<float>(mode | c->kernel_flags(mode), a, c->grid[mode], c->T, c->smem[mode], c->st);
 }
 
 // force / energy pass on a fresh list
@@ -1078,6 +1087,7 @@ extern "C" int dsdna_get_info(const dsdna_ctx* c, dsdna_info* info) {
   info->rebuilds = (int64_t)nb;
   cudaMemcpy(&nb, c->nlaunch, sizeof(nb), cudaMemcpyDeviceToHost);
   info->engine_launches = (int64_t)nb + c->host_launches;
+  info->rebuild_in_step = c->fused ? 1 : 0;
   info->grid_blocks = c->grid[MODE_STEP];
   info->block_threads = c->T;
   info->max_neighbors = c->p.max_neighbors;

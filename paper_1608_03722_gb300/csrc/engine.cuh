@@ -42,6 +42,7 @@ enum : unsigned {
 constexpr unsigned B_ERRMASK = B_EFENE | B_ENAN | B_EOVF | B_ETIMEOUT | B_EIMG;
 enum : int { MODE_STEP = 0, MODE_FORCES = 1, MODE_ENERGY = 2 };
 constexpr int MODE_EXT = 4;   // launch flag: kernel instance with circular molecules / bubble rule
+constexpr int MODE_FUSED = 8; // launch flag (MODE_STEP): instance that rebuilds the list in the kernel
 constexpr int NTERMS = 10;
 constexpr int EOUT_STRIDE = 16;           // energy terms + 6 virial
 constexpr float FIX_SCALE_F = 1.0f / 536870912.0f;  // 2^-29

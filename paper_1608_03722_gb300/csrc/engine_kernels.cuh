@@ -1,9 +1,10 @@
 // engine_kernels.cuh -- persistent step kernel of the dsDNA engine: the fused
 // force + Langevin strip pass and the step loop with its grid barrier (the
-// list rebuild is in rebuild.cuh).  Included by kern_mixed.cu (Real = float)
-// and kern_fp64.cu (Real = double).
+// list rebuild is in rebuild.cuh; small systems run it inside this kernel).
+// Included by kern_mixed.cu (Real = float) and kern_fp64.cu (Real = double).
 #pragma once
 #include "engine.cuh"
+#include "rebuild.cuh"
 
 namespace dsdna {
 
@@ -25,7 +26,7 @@ struct SegSmem {
 };
 
 template <class Real>
-__host__ __device__ inline size_t seg_warp_bytes() {
+__host__ __device__ constexpr size_t seg_warp_bytes() {
   size_t b = sizeof(SPos<Real>) * RING + sizeof(int) * RING;
   b = (b + 15) & ~(size_t)15;
   b += sizeof(Real) * (size_t)RING * 15;
@@ -572,6 +573,38 @@ __device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_
   __syncwarp();
 }
 
+// ---------------------------------------------------------------- list rebuild in the step kernel
+// The five phases of the rebuild kernels (bin, block sums, scan, scatter,
+// list), each over the whole persistent grid with a bounded grid barrier
+// after it, for systems small enough that kernel boundaries cost more than
+// the barriers.  The list phase keeps each lane's buffer in the warp's
+// shared ring, which the next step restages.  Linear and hashed tables.
+template <class Real>
+__device__ unsigned fused_rebuild(const KArgs<Real>& a, const SegSmem<Real>& sm, int cur, unsigned* s_word,
+                                  unsigned* s_red) {
+  static_assert(seg_warp_bytes<Real>() >= sizeof(int) * 32 * LIST_CAP, "list buffers must fit in a warp's ring");
+  unsigned fl = 0;
+  rebuild_bin(a, cur, fl);
+  unsigned r = grid_sync(a.bar, gridDim.x, fl, a.spin_budget, s_word);
+  if (r & B_ERRMASK) return r;
+  rebuild_scan_a(a, s_red);
+  r = grid_sync(a.bar, gridDim.x, 0u, a.spin_budget, s_word);
+  if (r & B_ERRMASK) return r;
+  rebuild_scan_b(a, s_red);
+  r = grid_sync(a.bar, gridDim.x, 0u, a.spin_budget, s_word);
+  if (r & B_ERRMASK) return r;
+  rebuild_scatter(a);
+  r = grid_sync(a.bar, gridDim.x, 0u, a.spin_budget, s_word);
+  if (r & B_ERRMASK) return r;
+  fl = 0;
+  int* list = reinterpret_cast<int*>(sm.pos) + (threadIdx.x & 31) * LIST_CAP;
+  if (a.table == TABLE_LINEAR) rebuild_list_lanes<Real>(a, fl, list);
+  else rebuild_list_lanes_hash<Real>(a, fl, list);
+  r = grid_sync(a.bar, gridDim.x, fl, a.spin_budget, s_word);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !(r & B_ERRMASK)) *a.nrebuild += 1;
+  return r;
+}
+
 // ---------------------------------------------------------------- persistent kernel
 // MODE_STEP: advance up to *steps_left steps (all of them when steps_left is
 // null: nsteps), one bounded grid barrier per step; stop early when a bead
@@ -579,8 +612,10 @@ __device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_
 // MODE_FORCES / MODE_ENERGY: one pass with the current list.
 // EXT: the instance for systems with circular molecules or the bubble rule
 // (junction pass, open-pair marks, removed terms); the other instance
-// compiles none of it.
-template <class Real, int MODE, int CAPMAX, bool EXT>
+// compiles none of it.  FUSED (MODE_STEP): a stale list is rebuilt inside the
+// kernel (fused_rebuild) and the steps go on, instead of returning so that
+// the rebuild kernels run.
+template <class Real, int MODE, int CAPMAX, bool EXT, bool FUSED = false>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 1) engine_kernel(const __grid_constant__ KArgs<Real> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned s_word;
@@ -614,7 +649,17 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 1) engine_kernel(
     const unsigned r = grid_sync(a.bar, gridDim.x, s_fl, a.spin_budget, &s_word);
     if (r & B_ERRMASK) { errbits = r; break; }
     ++done;
-    if (r & B_STALE) { need = 1; break; }
+    if (r & B_STALE) {
+      if constexpr (FUSED) {
+        __shared__ unsigned s_red[32];
+        const unsigned rr = fused_rebuild(a, sm, (int)((step + 1) & 1), &s_word, s_red);
+        if (rr & B_ERRMASK) { errbits = rr; break; }
+        continue;
+      } else {
+        need = 1;
+        break;
+      }
+    }
   }
   if (threadIdx.x == 0) {
     if (errbits & B_ERRMASK) atomicOr(a.err, errbits & B_ERRMASK);

@@ -10,18 +10,21 @@ namespace dsdna {
 
 constexpr int CAPMAX = 64;
 
-// mode | MODE_EXT selects the instance with circular molecules and the bubble rule.
+// mode | MODE_EXT selects the instance with circular molecules and the bubble
+// rule, MODE_STEP | MODE_FUSED the one that rebuilds the list in the kernel.
+template <class Real, bool EXT>
+static const void* engine_fn_ext(int mode) {
+  switch (mode & 3) {
+    case MODE_STEP:
+      return (mode & MODE_FUSED) ? (const void*)engine_kernel<Real, MODE_STEP, CAPMAX, EXT, true>
+                                 : (const void*)engine_kernel<Real, MODE_STEP, CAPMAX, EXT, false>;
+    case MODE_FORCES: return (const void*)engine_kernel<Real, MODE_FORCES, CAPMAX, EXT>;
+    default: return (const void*)engine_kernel<Real, MODE_ENERGY, CAPMAX, EXT>;
+  }
+}
 template <class Real>
 static const void* engine_fn(int mode) {
-  const bool ext = (mode & MODE_EXT) != 0;
-  switch (mode & ~MODE_EXT) {
-    case MODE_STEP: return ext ? (const void*)engine_kernel<Real, MODE_STEP, CAPMAX, true>
-                               : (const void*)engine_kernel<Real, MODE_STEP, CAPMAX, false>;
-    case MODE_FORCES: return ext ? (const void*)engine_kernel<Real, MODE_FORCES, CAPMAX, true>
-                                 : (const void*)engine_kernel<Real, MODE_FORCES, CAPMAX, false>;
-    default: return ext ? (const void*)engine_kernel<Real, MODE_ENERGY, CAPMAX, true>
-                        : (const void*)engine_kernel<Real, MODE_ENERGY, CAPMAX, false>;
-  }
+  return (mode & MODE_EXT) ? engine_fn_ext<Real, true>(mode) : engine_fn_ext<Real, false>(mode);
 }
 
 // Largest co-resident grid for the cooperative launch of `mode` with T threads.
@@ -47,18 +50,9 @@ cudaError_t engine_launch(int mode, const KArgs<Real>& a, int grid, int T, size_
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const bool ext = (mode & MODE_EXT) != 0;
-  switch (mode & ~MODE_EXT) {
-    case MODE_STEP:
-      return ext ? cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_STEP, CAPMAX, true>, a)
-                 : cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_STEP, CAPMAX, false>, a);
-    case MODE_FORCES:
-      return ext ? cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_FORCES, CAPMAX, true>, a)
-                 : cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_FORCES, CAPMAX, false>, a);
-    default:
-      return ext ? cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_ENERGY, CAPMAX, true>, a)
-                 : cudaLaunchKernelEx(&cfg, engine_kernel<Real, MODE_ENERGY, CAPMAX, false>, a);
-  }
+  // the instance chosen by mode, launched with its parameter block
+  void* args[] = {const_cast<KArgs<Real>*>(&a)};
+  return cudaLaunchKernelExC(&cfg, engine_fn<Real>(mode), args);
 }
 
 // The five rebuild kernels on stream st (grid-stride; the scan pair shares one grid).

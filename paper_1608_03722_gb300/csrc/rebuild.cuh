@@ -543,12 +543,10 @@ __device__ void rebuild_list_warps(const KArgs<Real>& a, unsigned& fl) {
 // image, the minimum image within the list radius because every edge has >= 3
 // cells of at least that radius.  Hits are inserted in partner-slot order
 // into the lane's buffer and then written.
+// `list`: this lane's LIST_CAP-entry buffer in shared memory.
 template <class Real>
-__device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl) {
-  __shared__ int sent[LIST_WARPS][32][LIST_CAP];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl, int* list) {
   const int JMASK = (1 << NBR_J_BITS) - 1;
-  int* list = sent[w][lane];
   const int nx = a.nc[0], ny = a.nc[1], nz = a.nc[2];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
@@ -638,11 +636,8 @@ __device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl) {
 // twice; beads of another block or molecule sharing a bucket fail the
 // distance or molecule test.
 template <class Real>
-__device__ void rebuild_list_lanes_hash(const KArgs<Real>& a, unsigned& fl) {
-  __shared__ int sent[LIST_WARPS][32][LIST_CAP];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ void rebuild_list_lanes_hash(const KArgs<Real>& a, unsigned& fl, int* list) {
   const int JMASK = (1 << NBR_J_BITS) - 1;
-  int* list = sent[w][lane];
   const unsigned bmask = (a.H >> 3) - 1u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
@@ -731,8 +726,9 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list(const KArgs<Re
 
 template <class Real>
 __global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list_lanes_hash(const KArgs<Real> a) {
+  __shared__ int sent[LIST_WARPS][32][LIST_CAP];
   unsigned fl = 0;
-  rebuild_list_lanes_hash<Real>(a, fl);
+  rebuild_list_lanes_hash<Real>(a, fl, sent[threadIdx.x >> 5][threadIdx.x & 31]);
   if (fl) atomicOr(a.err, fl & B_ERRMASK);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.rebuild = 0;
@@ -742,8 +738,9 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list_lanes_hash(con
 
 template <class Real>
 __global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list_lanes(const KArgs<Real> a) {
+  __shared__ int sent[LIST_WARPS][32][LIST_CAP];
   unsigned fl = 0;
-  rebuild_list_lanes<Real>(a, fl);
+  rebuild_list_lanes<Real>(a, fl, sent[threadIdx.x >> 5][threadIdx.x & 31]);
   if (fl) atomicOr(a.err, fl & B_ERRMASK);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.rebuild = 0;
