@@ -408,3 +408,29 @@ def test_open_box_list_with_shared_buckets_equals_brute_force(prec):
     assert lo <= got <= hi and len(lo) > 1000
     assert ctx.info()["cell_table"] == 8192      # 2^13 entries = 1024 buckets for 3200 beads
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("periodic", [False, True])
+def test_rebuild_in_the_step_kernel_follows_the_same_trajectory(prec, periodic):
+    """rebuild_mode 2 (list rebuilt inside the persistent step kernel) and 1
+    (separate rebuild kernels) build the same sorted lists, so 400 steps with
+    many rebuilds give bitwise the same state (open box: hashed table;
+    periodic: linear table)."""
+    if periodic:
+        cfg = dense_walk(1200, seed=13)
+        kw = dict(box=cfg.box)
+    else:
+        cfg = I.c4_batch(n_mol=6, lo=200, hi=600, seed=2)
+        kw = {}
+    out = []
+    for mode in (1, 2):
+        p = D.dsdna_default_params(precision=prec, rebuild_mode=mode, skin=0.1, seed=4, **kw)
+        ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether)
+        ctx.step(400)
+        info = ctx.info()
+        assert info["rebuild_in_step"] == (mode == 2) and info["rebuilds"] > 10
+        out.append(ctx.get_state())
+        ctx.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
