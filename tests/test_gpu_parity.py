@@ -9,7 +9,6 @@ with S_i the oracle's sum over all terms acting on the site of |term force|
 separately).  Mixed engine: rel = 1e-5, abs = 5e-4 kT/nm (twice the stiffest
 term, 2 K4 lambda^2 = 3840 kT/nm^2, times the FP32 spacing of a 0.5 nm
 displacement).  FP64 engine: rel = 1e-9, abs = 1e-10 kT/nm.
-(DESIGN.md, "Parity tolerances".)
 """
 import numpy as np
 import pytest
