@@ -27,16 +27,24 @@ def _call(L, p, n_bp, X, u, Fb, Fp, stream):
                                   C.c_void_p(stream))
 
 
-@pytest.mark.parametrize("which", ["periodic", "ragged"])
+@pytest.mark.parametrize("which", ["periodic", "ragged", "bubbles"])
 def test_noalloc_forces_equal_the_context_path_on_two_calls(which):
+    """Also with the Sec. 5 bubble rule on (open runs of 3-5 base pairs), which
+    the no-alloc call evaluates in the kernel instance that has it."""
     import torch
     assert torch.cuda.is_available()
+    kw = {}
     if which == "periodic":
         cfg = I.random_walk_helix(n_bp=3000, phi=0.15, clearance=1.7, seed=2)
     else:
         cfg = I.ragged_batch([700, 1, 129, 2500, 40], seed=6, spread=0.03)
+    if which == "bubbles":
+        for k in (10, 11, 12, 200, 201, 202, 203, 204, 900, 901, 902):
+            r = cfg.X[2 * k + 1] - cfg.X[2 * k]
+            cfg.X[2 * k + 1] += 0.5 * r / np.linalg.norm(r)
+        kw = dict(bubble_rule=1, R0=3.0)
     assert cfg.n_nt <= 16384
-    p = D.dsdna_default_params(box=cfg.box)
+    p = D.dsdna_default_params(box=cfg.box, **kw)
     ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om)
     Fb_ref, Fp_ref = ctx.compute_forces()
     Xs, _, us, _ = ctx.get_state()
@@ -59,7 +67,11 @@ def test_noalloc_forces_equal_the_context_path_on_two_calls(which):
         if call == 1:
             assert free_after == free_before, "the second call changed the free device memory"
         out.append((Fb.cpu().numpy(), Fp.cpu().numpy()))
-    Sb, Sp = O.force_scale(O.params(box=cfg.box) if cfg.box[0] > 0 else O.params(), cfg.n_bp, Xs, us)
+    po = O.params(box=cfg.box, **kw) if cfg.box[0] > 0 else O.params(**kw)
+    Sb, Sp = O.force_scale(po, cfg.n_bp, Xs, us)
+    if which == "bubbles":       # the rule removed terms here: the context path matches the oracle too
+        ro = O.forces(po, cfg.n_bp, Xs, us)
+        assert (np.linalg.norm(Fb_ref - ro["Fb"], axis=1) <= REL * Sb + ABS).all()
     for Fb, Fp in out:
         assert (np.linalg.norm(Fb - Fb_ref, axis=1) <= REL * Sb + ABS).all()
         assert (np.linalg.norm(Fp - Fp_ref, axis=1) <= REL * Sp + ABS).all()
