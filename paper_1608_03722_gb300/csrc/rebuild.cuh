@@ -652,23 +652,28 @@ __device__ void rebuild_list_lanes_hash(const KArgs<Real>& a, unsigned& fl, int*
     const bool split = (lo >> 3) != (hi >> 3);
     // part 0: cells lo .. (split ? block end : hi) of block lo/8; part 1 (split): cells hi/8*8 .. hi
     const unsigned a0 = (unsigned)(lo & 7), b0 = split ? 7u : (unsigned)(hi & 7), b1 = (unsigned)(hi & 7);
-    unsigned seen0[9], seen1[9];
     int cnt = 0, total = 0;
+    // every row's bucket first, then all range bounds in flight at once, then
+    // the walks (a row whose bucket an earlier row of this bead has is empty)
 #pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      const int y = cy + r % 3 - 1, z = cz + r / 3 - 1;
+    for (int part = 0; part < 2; ++part) {
+      if (part == 1 && !split) break;
+      const int bx = part == 0 ? (lo >> 3) : (hi >> 3);
+      const unsigned c0 = part == 0 ? a0 : 0u, c1 = part == 0 ? b0 : b1;
+      unsigned bk[9], u0[9], u1[9];
 #pragma unroll
-      for (int part = 0; part < 2; ++part) {
-        if (part == 1 && !split) continue;
-        const unsigned b = hash_block(mol, part == 0 ? (lo >> 3) : (hi >> 3), y, z) & bmask;
+      for (int r = 0; r < 9; ++r) {
+        const unsigned b = hash_block(mol, bx, cy + r % 3 - 1, cz + r / 3 - 1) & bmask;
         bool dup = false;
 #pragma unroll
-        for (int q = 0; q < r; ++q) dup = dup || (part == 0 ? seen0[q] : seen1[q]) == b;
-        if (part == 0) seen0[r] = b; else seen1[r] = b;
-        if (dup) continue;
-        const unsigned u0 = a.start[(b << 3) | (part == 0 ? a0 : 0u)];
-        const unsigned u1 = a.start[((b << 3) | (part == 0 ? b0 : b1)) + 1u];
-        for (unsigned u = u0; u < u1; ++u) {
+        for (int q = 0; q < r; ++q) dup = dup || bk[q] == b;
+        bk[r] = b;
+        u0[r] = dup ? 0u : a.start[(b << 3) | c0];
+        u1[r] = dup ? 0u : a.start[((b << 3) | c1) + 1u];
+      }
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        for (unsigned u = u0[r]; u < u1[r]; ++u) {
           const float4 o = a.cent[u];
           const int jw = __float_as_int(o.w), j = jw & JMASK;
           const float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
