@@ -297,7 +297,9 @@ void dsdna_destroy(dsdna_ctx* ctx);
  * the paper, which ran LAMMPS with hand-set neighbour settings, Sec. 6).
  * Runs trial_steps warm-up steps and trial_steps timed steps of the system
  * sys on temporary contexts for every candidate neighbour skin
- * (0.2 .. 0.6 nm), CTA size (128, 256) and persistent CTAs per SM, and writes
+ * (0.2 .. 0.6 nm), CTA size (128, 256) and persistent CTAs per SM (and, with
+ * rebuild_mode 0 and between a quarter and four times
+ * DSDNA_FUSED_REBUILD_MAX_NT nucleotides, both rebuild paths), and writes
  * to *best the copy of *base with the fastest choice (ns per
  * nucleotide-step in *best_ns, may be NULL).  The candidates change how
  * often the list is rebuilt and how work is spread, never the computed

@@ -1122,10 +1122,19 @@ extern "C" int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys,
   dsdna_params winner = *base;
   int tried = 0;
   std::string why;
+  // where the automatic choice of rebuild path is close (a quarter to four
+  // times its threshold), both paths are tried
+  int64_t n_nt = 0;
+  for (int m = 0; m < sys->n_mol; ++m) n_nt += 2 * (int64_t)std::max(0, sys->n_bp[m]);
+  std::vector<int> modes{base->rebuild_mode};
+  if (base->rebuild_mode == 0 && n_nt >= DSDNA_FUSED_REBUILD_MAX_NT / 4 && n_nt <= 4 * (int64_t)DSDNA_FUSED_REBUILD_MAX_NT)
+    modes = {1, 2};
+  for (int rm : modes)
   for (double sk : skins)
     for (int T : blocks)
       for (int ps : per_sm) {
         dsdna_params p = *base;
+        p.rebuild_mode = rm;
         p.skin = sk;
         p.block_threads = T;
         p.blocks_per_sm = ps;
