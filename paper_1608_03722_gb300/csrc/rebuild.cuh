@@ -640,11 +640,13 @@ __device__ void rebuild_list_lanes_hash(const KArgs<Real>& a, unsigned& fl, int*
   const int JMASK = (1 << NBR_J_BITS) - 1;
   const unsigned bmask = (a.H >> 3) - 1u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
-    const float4 me = a.cent[t];
-    const int gw = __float_as_int(me.w), g = gw & JMASK;
-    const bool st_g = (gw >> NBR_J_BITS) & 1;
-    const int mol = __float_as_int(a.wpos[g].w);
+  // beads in slot (chain) order: neighbouring lanes are neighbours in space,
+  // so they share rows and candidates in cache and have similar work (the
+  // table order of a hashed table scatters them)
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.n; g += stride) {
+    const float4 me = a.wpos[g];
+    const bool st_g = (a.topo[g] & F_STERIC) != 0;
+    const int mol = __float_as_int(me.w);
     const int cx = (int)floorf(me.x * a.invcellh[0]);
     const int cy = (int)floorf(me.y * a.invcellh[1]);
     const int cz = (int)floorf(me.z * a.invcellh[2]);
