@@ -24,6 +24,10 @@
  *   - Denaturation (Sec. 5): per-pair hydrogen-bond stiffness (A.T / G.C) and
  *     the bubble rule that drops dihedral and bending terms inside runs of
  *     more than two open base pairs (dsdna_params.bubble_rule, K2_gc).
+ *   - Circular molecules (Sec. 6, Fig. 10): each strand closed on itself, so
+ *     the linking number is fixed by the initial state (dsdna_system.circular).
+ *   - Many independent molecules in one context (batched engine), stepped by
+ *     one persistent kernel per CUDA-graph chunk of steps.
  *
  * Layout of host arrays: AoS, X[3*g + c], with nucleotide slot
  * g = 2*(bp_offset(mol) + k) + s; s = 0 is strand A nucleotide k, s = 1 its
