@@ -463,6 +463,13 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       }
       Vd[0] = a.V[g]; Vd[1] = a.V[a.ns + g]; Vd[2] = a.V[2 * a.ns + g];
       V3<Real> Om{a.Om[g], a.Om[a.ns + g], a.Om[2 * a.ns + g]};
+      // the rebuild reference and the image word, loaded with the state and
+      // ahead of its stores (which the compiler cannot move them across)
+      int kr[3] = {0, 0, 0}, packed = 0;
+      if constexpr (MODE == MODE_STEP) {
+        kr[0] = a.kref[g]; kr[1] = a.kref[a.ns + g]; kr[2] = a.kref[2 * a.ns + g];
+        if constexpr (sizeof(Real) == 4) packed = a.Kw[(size_t)cur * a.ns + g].w;
+      }
       const bool frozen = (f & F_FROZEN) != 0;
       V3<Real> Ft{0, 0, 0}, Tt{0, 0, 0};
       if (!frozen) {
@@ -520,15 +527,13 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
             a.X[g] = Xd[0]; a.X[a.ns + g] = Xd[1]; a.X[2 * a.ns + g] = Xd[2];
           }
         }
-        int packed = 0;
-        if constexpr (sizeof(Real) == 4) packed = a.Kw[(size_t)cur * a.ns + g].w;
         const int k0 = fix32(Xd[0]), k1 = fix32(Xd[1]), k2 = fix32(Xd[2]);
         store_state(a, nxt, g, k0, k1, k2, Xd, un, packed);
         // rebuild trigger: a bead moved more than skin/2 since the last build
         const float hf = (float)h;
-        const float ddx = fixdiff(a.kref[g], k0 + bead_off(hf * (float)un.x));
-        const float ddy = fixdiff(a.kref[a.ns + g], k1 + bead_off(hf * (float)un.y));
-        const float ddz = fixdiff(a.kref[2 * a.ns + g], k2 + bead_off(hf * (float)un.z));
+        const float ddx = fixdiff(kr[0], k0 + bead_off(hf * (float)un.x));
+        const float ddy = fixdiff(kr[1], k1 + bead_off(hf * (float)un.y));
+        const float ddz = fixdiff(kr[2], k2 + bead_off(hf * (float)un.z));
         if (ddx * ddx + ddy * ddy + ddz * ddz > a.c.skin_half2) fl |= B_STALE;
       }
     }
