@@ -417,13 +417,13 @@ def main():
     nbar = 2.0 * len(ctx.neighbor_pairs()) / cfg.n_nt
 
     # algorithmic bytes per nucleotide-step of the fused force + Langevin kernel:
-    # mixed: read X, V (FP64 24 + 24), Omega (FP32 12), kref 12, mirror + orientation
-    # (16 + 16), topology 4, count 4, image 4 (periodic), list 4 n; write X, V, Omega,
-    # next mirror + orientation (24 + 24 + 12 + 16 + 16).  FP64: X, u, V, Omega 24 each
-    # read and written, kref 12, topology, count, image 4 each.
+    # mixed: read X, V (FP64 24 + 24), Omega (FP32 12), kref 12, mirror (its fourth word
+    # carries the periodic image) + orientation (16 + 16), topology 4, count 4, list 4 n;
+    # write X, V, Omega, next mirror + orientation (24 + 24 + 12 + 16 + 16).  FP64: X, u,
+    # V, Omega 24 each read and written, kref 12, topology, count, image (periodic) 4 each.
     periodic = 1 if cfg.box[0] > 0 else 0
     if prec == D.PREC_MIXED:
-        b_nt = (112 + 4 * periodic) + 92 + 4 * nbar
+        b_nt = 112 + 92 + 4 * nbar
     else:
         b_nt = (96 + 12 + 8 + 4 * periodic) + 96 + 4 * nbar
     steps_per_launch = prof["steps"] / max(prof["engine_launches"], 1)

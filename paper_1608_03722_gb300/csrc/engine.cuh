@@ -454,7 +454,7 @@ __device__ __forceinline__ unsigned grid_sync(GridBar* bar, unsigned nblocks,
       }
     }
     __threadfence();
-    res |= atomicOr(&bar->acc[g % 3], 0u);
+    res |= ld_acquire(&bar->acc[g % 3]);   // final once gen moved on; a load, not a serialised atomic
     *s_word = res;
   }
   __syncthreads();

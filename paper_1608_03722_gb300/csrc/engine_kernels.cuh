@@ -386,7 +386,10 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
     // typed WCA pairs (App. A Eq. 11) from the neighbour list
     {
       const int nn = a.ncnt[g];
-      const int img_me = a.periodic ? a.img[g] : 0;
+      // own periodic image: in mixed precision the image word of the mirror
+      // (Kw.w, staged a tile ago and still cached); the FP64 path keeps it apart
+      int img_me = 0;
+      if (a.periodic) img_me = sizeof(Real) == 4 ? a.Kw[(size_t)cur * a.ns + g].w : a.img[g];
       for (int q = 0; q < nn; ++q) {
         const int ent = a.nbr[(size_t)q * a.ns + g];
         const int j = ent & ENT_JMASK;
@@ -468,7 +471,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       int kr[3] = {0, 0, 0}, packed = 0;
       if constexpr (MODE == MODE_STEP) {
         kr[0] = a.kref[g]; kr[1] = a.kref[a.ns + g]; kr[2] = a.kref[2 * a.ns + g];
-        if constexpr (sizeof(Real) == 4) packed = a.Kw[(size_t)cur * a.ns + g].w;
+        if constexpr (sizeof(Real) == 4) packed = a.periodic ? a.Kw[(size_t)cur * a.ns + g].w : 0;
       }
       const bool frozen = (f & F_FROZEN) != 0;
       V3<Real> Ft{0, 0, 0}, Tt{0, 0, 0};

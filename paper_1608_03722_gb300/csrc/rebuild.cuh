@@ -109,7 +109,7 @@ __device__ void rebuild_bin(const KArgs<Real>& a, int cur, unsigned& fl) {
     const unsigned k = cell_key(a, mol, ci[0], ci[1], ci[2]);
     a.key[g] = (int)k;
     a.wpos[g] = make_float4(pw[0], pw[1], pw[2], __int_as_float(mol));
-    a.img[g] = packed;
+    if constexpr (sizeof(Real) == 8) a.img[g] = packed;   // mixed precision keeps it in Kw.w
     atomicAdd(&a.cnt[k], 1u);
     // build-time bead position on the fixed-point grid, for the rebuild trigger
     const float h = (float)a.c.h;
