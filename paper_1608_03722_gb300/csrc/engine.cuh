@@ -304,8 +304,9 @@ __device__ __forceinline__ int bead_off(float hu) { return __float2int_rn(-hu * 
 template <class Real>
 __device__ __forceinline__ void load_slot(const KArgs<Real>& a, int cur, int64_t g, SPos<Real>& s) {
   if constexpr (sizeof(Real) == 4) {
-    const int4 k = a.Kw[(size_t)cur * a.ns + g];
-    const float4 u = a.U[(size_t)cur * a.ns + g];
+    const unsigned i = (unsigned)cur * (unsigned)a.ns + (unsigned)g;   // below 2^27
+    const int4 k = a.Kw[i];
+    const float4 u = a.U[i];
     s.kx = k.x; s.ky = k.y; s.kz = k.z;
     s.ux = u.x; s.uy = u.y; s.uz = u.z;
   } else {

@@ -293,7 +293,7 @@ __device__ __forceinline__ void stage_slot(const KArgs<Real>& a, const SegSmem<R
   const int ri = ring(g);
   if (g >= 0 && g < a.n) {
     load_slot(a, cur, g, sm.pos[ri]);
-    sm.flg[ri] = a.topo[g];
+    sm.flg[ri] = a.topo[(unsigned)g];
   } else {
     sm.flg[ri] = 0;
   }
@@ -319,14 +319,15 @@ __device__ __forceinline__ void owner_pass(const KArgs<Real>& a, const SegSmem<R
 template <class Real>
 __device__ __forceinline__ void store_state(const KArgs<Real>& a, int nxt, int64_t g, int k0, int k1, int k2,
                                             const double* X, V3<Real> u, int packed) {
+  const unsigned ns = (unsigned)a.ns, gu = (unsigned)g;   // slot indices stay below 2^26
   if constexpr (sizeof(Real) == 4) {
-    a.Kw[(size_t)nxt * a.ns + g] = make_int4(k0, k1, k2, packed);
-    a.U[(size_t)nxt * a.ns + g] = make_float4(u.x, u.y, u.z, 0.0f);
+    a.Kw[(unsigned)nxt * ns + gu] = make_int4(k0, k1, k2, packed);
+    a.U[(unsigned)nxt * ns + gu] = make_float4(u.x, u.y, u.z, 0.0f);
   } else {
     double* Xo = a.X + (size_t)nxt * 3 * a.ns;
     double* uo = a.ud + (size_t)nxt * 3 * a.ns;
-    Xo[g] = X[0]; Xo[a.ns + g] = X[1]; Xo[2 * a.ns + g] = X[2];
-    uo[g] = u.x; uo[a.ns + g] = u.y; uo[2 * a.ns + g] = u.z;
+    Xo[gu] = X[0]; Xo[ns + gu] = X[1]; Xo[2 * ns + gu] = X[2];
+    uo[gu] = u.x; uo[ns + gu] = u.y; uo[2 * ns + gu] = u.z;
   }
 }
 
@@ -337,6 +338,7 @@ template <class Real, int MODE>
 __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t g, int cur,
                                                 int64_t step, unsigned& fl) {
   const int nxt = cur ^ 1;
+  const unsigned ns = (unsigned)a.ns, gu = (unsigned)g;   // slot indices stay below 2^26: 32-bit index arithmetic
   Real Eb[NTERMS];
   Real Wb[6];
   if constexpr (MODE == MODE_ENERGY) {
@@ -385,19 +387,19 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
     }
     // typed WCA pairs (App. A Eq. 11) from the neighbour list
     {
-      const int nn = a.ncnt[g];
+      const int nn = a.ncnt[gu];
       // own periodic image: in mixed precision the image word of the mirror
       // (Kw.w, staged a tile ago and still cached); the FP64 path keeps it apart
       int img_me = 0;
-      if (a.periodic) img_me = sizeof(Real) == 4 ? a.Kw[(size_t)cur * a.ns + g].w : a.img[g];
+      if (a.periodic) img_me = sizeof(Real) == 4 ? a.Kw[(unsigned)cur * ns + gu].w : a.img[gu];
       for (int q = 0; q < nn; ++q) {
-        const int ent = a.nbr[(size_t)q * a.ns + g];
+        const int ent = a.nbr[(unsigned)q * ns + gu];
         const int j = ent & ENT_JMASK;
         V3<Real> R;
         V3<Real> uj;
         if constexpr (sizeof(Real) == 4) {
-          const int4 kj = a.Kw[(size_t)cur * a.ns + j];
-          const float4 u4 = a.U[(size_t)cur * a.ns + j];
+          const int4 kj = a.Kw[(unsigned)cur * ns + (unsigned)j];
+          const float4 u4 = a.U[(unsigned)cur * ns + (unsigned)j];
           uj = V3<float>{u4.x, u4.y, u4.z};
           unsigned dx = (unsigned)kj.x - (unsigned)me.kx, dy = (unsigned)kj.y - (unsigned)me.ky,
                    dz = (unsigned)kj.z - (unsigned)me.kz;
@@ -411,8 +413,8 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
         } else {
           const double* X = a.X + (size_t)cur * 3 * a.ns;
           const double* ud = a.ud + (size_t)cur * 3 * a.ns;
-          uj = V3<double>{ud[j], ud[a.ns + j], ud[2 * a.ns + j]};
-          R = V3<double>{X[j] - me.x, X[a.ns + j] - me.y, X[2 * a.ns + j] - me.z};
+          uj = V3<double>{ud[(unsigned)j], ud[ns + (unsigned)j], ud[2 * ns + (unsigned)j]};
+          R = V3<double>{X[(unsigned)j] - me.x, X[ns + (unsigned)j] - me.y, X[2 * ns + (unsigned)j] - me.z};
           if (a.periodic) {
             const int ij = a.img[j];
             R.x += (double)(img_comp(img_me, 0) - img_comp(ij, 0) + ent_shift(ent, 0)) * a.L[0];
@@ -460,18 +462,18 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       const uint32_t local = (uint32_t)(g - 2 * a.mol_off[mol]);
       double Xd[3], Vd[3];
       if constexpr (sizeof(Real) == 4) {
-        Xd[0] = a.X[g]; Xd[1] = a.X[a.ns + g]; Xd[2] = a.X[2 * a.ns + g];
+        Xd[0] = a.X[gu]; Xd[1] = a.X[ns + gu]; Xd[2] = a.X[2 * ns + gu];
       } else {
         Xd[0] = me.x; Xd[1] = me.y; Xd[2] = me.z;
       }
-      Vd[0] = a.V[g]; Vd[1] = a.V[a.ns + g]; Vd[2] = a.V[2 * a.ns + g];
-      V3<Real> Om{a.Om[g], a.Om[a.ns + g], a.Om[2 * a.ns + g]};
+      Vd[0] = a.V[gu]; Vd[1] = a.V[ns + gu]; Vd[2] = a.V[2 * ns + gu];
+      V3<Real> Om{a.Om[gu], a.Om[ns + gu], a.Om[2 * ns + gu]};
       // the rebuild reference and the image word, loaded with the state and
       // ahead of its stores (which the compiler cannot move them across)
       int kr[3] = {0, 0, 0}, packed = 0;
       if constexpr (MODE == MODE_STEP) {
-        kr[0] = a.kref[g]; kr[1] = a.kref[a.ns + g]; kr[2] = a.kref[2 * a.ns + g];
-        if constexpr (sizeof(Real) == 4) packed = a.periodic ? a.Kw[(size_t)cur * a.ns + g].w : 0;
+        kr[0] = a.kref[gu]; kr[1] = a.kref[ns + gu]; kr[2] = a.kref[2 * ns + gu];
+        if constexpr (sizeof(Real) == 4) packed = a.periodic ? a.Kw[(unsigned)cur * ns + gu].w : 0;
       }
       const bool frozen = (f & F_FROZEN) != 0;
       V3<Real> Ft{0, 0, 0}, Tt{0, 0, 0};
@@ -524,10 +526,10 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
           if (!(isfinite(Ft.x) && isfinite(Ft.y) && isfinite(Ft.z) && isfinite(Om.x) && isfinite(Om.y) &&
                 isfinite(Om.z)))
             fl |= B_ENAN;
-          a.V[g] = Vd[0]; a.V[a.ns + g] = Vd[1]; a.V[2 * a.ns + g] = Vd[2];
-          a.Om[g] = Om.x; a.Om[a.ns + g] = Om.y; a.Om[2 * a.ns + g] = Om.z;
+          a.V[gu] = Vd[0]; a.V[ns + gu] = Vd[1]; a.V[2 * ns + gu] = Vd[2];
+          a.Om[gu] = Om.x; a.Om[ns + gu] = Om.y; a.Om[2 * ns + gu] = Om.z;
           if constexpr (sizeof(Real) == 4) {
-            a.X[g] = Xd[0]; a.X[a.ns + g] = Xd[1]; a.X[2 * a.ns + g] = Xd[2];
+            a.X[gu] = Xd[0]; a.X[ns + gu] = Xd[1]; a.X[2 * ns + gu] = Xd[2];
           }
         }
         const int k0 = fix32(Xd[0]), k1 = fix32(Xd[1]), k2 = fix32(Xd[2]);
