@@ -33,6 +33,12 @@ __device__ __forceinline__ unsigned hash_block(int mol, int bx, int cy, int cz) 
   return h;
 }
 
+// The x-blocks of the hashed table start at cell 4 (mod 8): a molecule held
+// along an axis through the origin (the anchored single-molecule set-ups of
+// Sec. 4) spans x-cells -1 and 0 and so stays inside one block, whose rows
+// are then one range each.
+constexpr int HASH_X_OFF = 4;
+
 template <class Real>
 __device__ __forceinline__ unsigned cell_key(const KArgs<Real>& a, int mol, int cx, int cy, int cz) {
   if (a.table == TABLE_LINEAR) return (unsigned)cx + (unsigned)a.nc[0] * ((unsigned)cy + (unsigned)a.nc[1] * (unsigned)cz);
@@ -44,7 +50,8 @@ __device__ __forceinline__ unsigned cell_key(const KArgs<Real>& a, int mol, int 
   // x-neighbour cells is one range of the sorted beads (two across a block
   // edge).  Distinct blocks may share a bucket; the list build skips a range
   // it has already walked.
-  return (hash_block(mol, cx >> 3, cy, cz) & ((a.H >> 3) - 1u)) << 3 | (unsigned)(cx & 7);
+  const int xs = cx + HASH_X_OFF;
+  return (hash_block(mol, xs >> 3, cy, cz) & ((a.H >> 3) - 1u)) << 3 | (unsigned)(xs & 7);
 }
 
 template <class Real>
@@ -650,7 +657,7 @@ __device__ void rebuild_list_lanes_hash(const KArgs<Real>& a, unsigned& fl, int*
     const int cx = (int)floorf(me.x * a.invcellh[0]);
     const int cy = (int)floorf(me.y * a.invcellh[1]);
     const int cz = (int)floorf(me.z * a.invcellh[2]);
-    const int lo = cx - 1, hi = cx + 1;
+    const int lo = cx - 1 + HASH_X_OFF, hi = cx + 1 + HASH_X_OFF;   // block coordinates, as cell_key
     const bool split = (lo >> 3) != (hi >> 3);
     // part 0: cells lo .. (split ? block end : hi) of block lo/8; part 1 (split): cells hi/8*8 .. hi
     const unsigned a0 = (unsigned)(lo & 7), b0 = split ? 7u : (unsigned)(hi & 7), b1 = (unsigned)(hi & 7);
