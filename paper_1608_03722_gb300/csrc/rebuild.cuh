@@ -680,10 +680,21 @@ __device__ void rebuild_list_lanes_hash(const KArgs<Real>& a, unsigned& fl, int*
         u0[r] = dup ? 0u : a.start[(b << 3) | c0];
         u1[r] = dup ? 0u : a.start[((b << 3) | c1) + 1u];
       }
+      // the 9 ranges as one stream of candidates: a warp runs as many
+      // iterations as its busiest lane has candidates (plus 9 range switches),
+      // not the sum over rows of each row's longest range
+      int r = 0;
+      unsigned u = u0[0], e = u1[0];
+      for (;;) {
+        if (u >= e) {
+          if (++r == 9) break;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) {
-        for (unsigned u = u0[r]; u < u1[r]; ++u) {
-          const float4 o = a.cent[u];
+          for (int q = 1; q < 9; ++q)
+            if (q == r) { u = u0[q]; e = u1[q]; }
+          continue;
+        }
+        {
+          const float4 o = a.cent[u++];
           const int jw = __float_as_int(o.w), j = jw & JMASK;
           const float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
           const float r2 = dx * dx + dy * dy + dz * dz;
