@@ -410,6 +410,37 @@ def test_open_box_list_with_shared_buckets_equals_brute_force(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_open_box_list_across_hash_blocks_equals_brute_force(prec):
+    """Open box, molecules spread over the hashed table's x-blocks of 8 cells:
+    worm-like molecules with their origins at negative and positive x and y
+    (some on block edges), one held along z through the origin (x-cells -1
+    and 0, inside one block), one lying along x across many blocks.  The list
+    holds each pair once and exactly the brute-force set."""
+    rng = np.random.default_rng(11)
+    Xs, us = [], []
+    for k in range(5):
+        X, u = I.wlc_helix(300, 40.0, rng, origin=(rng.uniform(-40.0, 40.0), rng.uniform(-40.0, 40.0), 0.0))
+        Xs.append(X); us.append(u)
+    X, u = I.straight_helix(300)
+    Xs.append(X); us.append(u)
+    R = np.array([[0.0, 0.0, 1.0], [0.0, 1.0, 0.0], [-1.0, 0.0, 0.0]])   # a quarter turn about y: z -> x
+    X, u = I.straight_helix(300, origin=(0.0, 0.0, -50.0))
+    Xs.append(X @ R.T); us.append(u @ R.T)
+    X = np.concatenate(Xs); u = np.concatenate(us)
+    n_bp = [300] * 7
+    ctx = D.Context(D.dsdna_default_params(precision=prec), n_bp, X=X, u=u)
+    pl = ctx.neighbor_pairs()
+    got = {tuple(x) for x in pl}
+    assert len(pl) == len(got), "a pair listed twice"
+    skin = ctx.params.skin + 0.01
+    lo = {tuple(x) for x in O.pairs(O.params(), n_bp, X, u, extra=skin - 1e-4)}
+    hi = {tuple(x) for x in O.pairs(O.params(), n_bp, X, u, extra=skin + 1e-4)}
+    assert lo <= got <= hi and len(lo) > 1000
+    assert X[:, 0].min() < -20.0 and X[:, 0].max() > 20.0   # the molecules span many x-blocks
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("periodic", [False, True])
 def test_rebuild_in_the_step_kernel_follows_the_same_trajectory(prec, periodic):
     """rebuild_mode 2 (list rebuilt inside the persistent step kernel) and 1
