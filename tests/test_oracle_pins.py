@@ -175,6 +175,64 @@ def test_planarity_minimum_at_ninety_degrees():
         assert _E(p, N, X, u)[6] > 0.0
 
 
+def _morse_energy(p, rise):
+    """Morse energy (App. A Eq. 13) of a straight 2 bp duplex whose patches are
+    `rise` apart along the axis: two patch-patch pairs, one per strand."""
+    X, u = I.straight_helix(2)
+    X[:, 2] *= rise / I.RISE
+    return _E(p, 2, X, u)[5]
+
+
+def test_morse_amplitude_range_and_stiffness():
+    """App. A Eq. 13 with Table 1 (K4 = 30, lambda = 8, r0 = 0.34): the well is
+    K4 deep (the energy of two separated patches), the energy at
+    r0 + ln(2)/lambda, where the exponential has halved, is K4/4, and the
+    curvature at r0 is 2 K4 lambda^2.  A Morse amplitude off by any factor, or
+    a wrong range, fails one of these."""
+    p = O.params(R0=10.0)          # a wide FENE bond, so the stretched backbone stays bonded
+    far = _morse_energy(p, 3.0)
+    assert abs(far - 2 * 30.0) < 1e-6, far                      # two pairs, each K4 away from the well
+    half = _morse_energy(p, 0.34 + math.log(2.0) / 8.0)
+    assert abs(half - 2 * 30.0 / 4) < 1e-9, half
+    h = 1e-4
+    curv = (_morse_energy(p, 0.34 + h) + _morse_energy(p, 0.34 - h) - 2 * _morse_energy(p, 0.34)) / h ** 2
+    assert abs(curv / 2 - 2 * 30.0 * 64.0) < 1e-4 * 3840.0, curv
+
+
+def _planar_energy(p, alpha):
+    """Planarity energy (App. A Eq. 14) of one strand step whose angle E-F-B
+    (vertex at patch F of nucleotide 1, between patch E of nucleotide 0 and
+    bead B of nucleotide 1) is alpha; strand B sits 50 nm away as a relaxed
+    helix (its angle is 90 degrees, zero energy)."""
+    X, u = I.straight_helix(2)
+    pe, pf = np.array([0.0, 0.0, 0.0]), np.array([0.0, 0.0, I.RISE])
+    b0 = pe + np.array([I.ELL, 0.0, 0.0])
+    b1 = pf + I.ELL * np.array([math.sin(alpha), 0.0, -math.cos(alpha)])   # angle alpha to pe - pf = -z
+    for g, (bead, patch) in ((0, (b0, pe)), (2, (b1, pf))):
+        X[g] = 0.5 * (bead + patch)
+        u[g] = (patch - bead) / np.linalg.norm(patch - bead)
+    X[1::2, 0] += 50.0
+    return _E(p, 2, X, u)[6]
+
+
+def test_planarity_amplitude_and_form():
+    """App. A Eq. 14 with Table 1 (K5 = 200, alpha0 = 90 deg): harmonic in the
+    angle itself with the printed 1/2, so the energy is (K5/2)(pi/2)^2 with the
+    three sites in a line (alpha = 0 or 180 deg), a quarter of that at 45 and
+    135 deg (a harmonic form in cos(alpha) would give half), and the curvature
+    at 90 deg is K5.  A factor K5 in place of K5/2 doubles every value."""
+    p = O.params(R0=10.0)
+    top = 100.0 * (math.pi / 2) ** 2
+    for a in (0.0, math.pi):
+        assert abs(_planar_energy(p, a) - top) < 1e-9 * top, (a, _planar_energy(p, a))
+    for a in (math.pi / 4, 3 * math.pi / 4):
+        assert abs(_planar_energy(p, a) - top / 4) < 1e-9 * top, (a, _planar_energy(p, a))
+    assert abs(_planar_energy(p, math.pi / 2)) < 1e-12
+    d = 1e-4
+    curv = (_planar_energy(p, math.pi / 2 + d) + _planar_energy(p, math.pi / 2 - d)) / d ** 2
+    assert abs(curv - 200.0) < 1e-6 * 200.0, curv
+
+
 def test_bending_zero_straight_and_maximal_folded():
     p = O.params()
     X, u = I.straight_helix(3)
