@@ -116,7 +116,7 @@ typedef struct dsdna_params {
   double kT, gamma, dt;                  /* Langevin temperature, friction per site, time step */
   uint64_t seed;                         /* Philox key */
   int noise;                             /* DSDNA_NOISE_* */
-  int steric_phase;                      /* steric iff (index along strand from its 5' end) % 3 == phase */
+  int steric_phase;                      /* steric iff (index along strand from its 5' end) % 3 == phase (0, 1 or 2) */
   double box[3];                         /* > 0: periodic edge in that direction; <= 0: open */
   double skin;                           /* neighbour-list skin, at most 1 nm (0: default 0.3) */
   int precision;                         /* DSDNA_PREC_MIXED (FP32 forces, FP64 X/V) or DSDNA_PREC_FP64 */
@@ -327,7 +327,10 @@ int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys, const dsdn
  * Limits: at most DSDNA_NOALLOC_MAX_NT nucleotides and DSDNA_NOALLOC_MAX_MOL
  * molecules; a periodic box may span at most 32 cells of edge
  * 2^(1/6) max(sigma) + skin per direction; precision must be
- * DSDNA_PREC_MIXED.  Larger inputs return DSDNA_EINVAL.
+ * DSDNA_PREC_MIXED.  Larger inputs return DSDNA_EINVAL, and so do the
+ * parameters dsdna_create rejects (skin outside [0, 1] nm, bubble_rule or
+ * steric_phase out of range, non-positive ell, R0 or rc_hb, negative K2_gc);
+ * skin 0 means the default 0.3 nm, as in dsdna_create.
  *
  * Scratch memory: one fixed device array of about 5 MB (cell table,
  * neighbour list, position mirrors), reserved on every GPU that loads the

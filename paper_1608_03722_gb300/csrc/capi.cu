@@ -356,6 +356,7 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
   if (p->rebuild_mode < 0 || p->rebuild_mode > 2) return fail(nullptr, DSDNA_EINVAL, "rebuild_mode must be 0, 1 or 2");
   if (p->K2_gc < 0.0) return fail(nullptr, DSDNA_EINVAL, "K2_gc must be >= 0");
   if (p->noise < 0 || p->noise > 2) return fail(nullptr, DSDNA_EINVAL, "noise mode");
+  if (p->steric_phase < 0 || p->steric_phase > 2) return fail(nullptr, DSDNA_EINVAL, "steric_phase must be 0, 1 or 2");
   if (p->skin < 0.0 || p->skin > 1.0) return fail(nullptr, DSDNA_EINVAL, "skin must be in [0, 1] nm");
   if (p->max_neighbors < 0 || p->max_neighbors > 32) return fail(nullptr, DSDNA_EINVAL, "max_neighbors must be <= 32");
   if (p->block_threads && (p->block_threads < 64 || p->block_threads > 256 || p->block_threads % 32))

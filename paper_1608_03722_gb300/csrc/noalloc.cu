@@ -156,6 +156,12 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   if (!p || !n_bp || !X || !u || !F_bead || !F_patch) return na_fail(DSDNA_EINVAL, "null argument");
   if (n_mol < 1 || n_mol > NA_MAX_MOL) return na_fail(DSDNA_EINVAL, "n_mol must be in [1, DSDNA_NOALLOC_MAX_MOL]");
   if (p->precision != DSDNA_PREC_MIXED) return na_fail(DSDNA_EINVAL, "only the mixed-precision force pass has a no-alloc variant");
+  // the checks dsdna_create makes on the parameters this call uses
+  if (p->skin < 0.0 || p->skin > 1.0) return na_fail(DSDNA_EINVAL, "skin must be in [0, 1] nm");
+  if (p->bubble_rule < 0 || p->bubble_rule > 2) return na_fail(DSDNA_EINVAL, "bubble_rule must be 0, 1 or 2");
+  if (p->steric_phase < 0 || p->steric_phase > 2) return na_fail(DSDNA_EINVAL, "steric_phase must be 0, 1 or 2");
+  if (!(p->ell > 0.0) || !(p->R0 > 0.0) || !(p->rc_hb > 0.0)) return na_fail(DSDNA_EINVAL, "non-positive ell/R0/rc");
+  if (p->K2_gc < 0.0) return na_fail(DSDNA_EINVAL, "K2_gc must be >= 0");
   int64_t mol_off[NA_MAX_MOL + 1];
   mol_off[0] = 0;
   for (int m = 0; m < n_mol; ++m) {
@@ -164,7 +170,9 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   }
   const int64_t n = 2 * mol_off[n_mol];
   if (n > NA_MAX_NT) return na_fail(DSDNA_EINVAL, "more nucleotides than DSDNA_NOALLOC_MAX_NT");
-  const double skin = p->skin > 0.0 ? p->skin : 0.3;
+  dsdna_params q = *p;          // skin 0 means the default, as in dsdna_create
+  if (q.skin == 0.0) q.skin = 0.3;
+  const double skin = q.skin;
   const double rc6 = std::pow(2.0, 1.0 / 6.0);
   const double cellh = (rc6 * std::max(p->sigma_ss, p->sigma_cross) + skin + 0.01) * 1.0001;
   const bool periodic = p->box[0] > 0.0;
@@ -202,7 +210,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   unsigned char* b = s->base;
 
   KArgs<float> a{};
-  fill_coef_mixed(*p, a.c);
+  fill_coef_mixed(q, a.c);   // list radius from the same skin as the cell edge
   a.n = n; a.ns = NA_MAX_NT; a.n_mol = n_mol; a.nseg = (n + 31) / 32; a.cap = NA_CAP;
   a.nsteps = 0; a.noise_mode = 0; a.seed_lo = 0; a.seed_hi = 0;
   a.bubble = p->bubble_rule ? 1 : 0;   // one evaluation without history: rule 2 removes what rule 1 does

@@ -27,15 +27,21 @@ def _call(L, p, n_bp, X, u, Fb, Fp, stream):
                                   C.c_void_p(stream))
 
 
-@pytest.mark.parametrize("which", ["periodic", "ragged", "bubbles"])
+@pytest.mark.parametrize("which", ["periodic", "ragged", "bubbles", "small_box"])
 def test_noalloc_forces_equal_the_context_path_on_two_calls(which):
-    """Also with the Sec. 5 bubble rule on (open runs of 3-5 base pairs), which
-    the no-alloc call evaluates in the kernel instance that has it."""
+    """Periodic box with a linear cell table, open box with the hashed table,
+    a periodic box with fewer than 3 cells on one edge (the Morton table:
+    molecules meet their own periodic images along z), and the Sec. 5 bubble
+    rule on (open runs of 3-5 base pairs), which the no-alloc call evaluates
+    in the kernel instance that has it."""
     import torch
     assert torch.cuda.is_available()
     kw = {}
     if which == "periodic":
         cfg = I.random_walk_helix(n_bp=3000, phi=0.15, clearance=1.7, seed=2)
+    elif which == "small_box":
+        cfg = I.ragged_batch([10, 6, 9], seed=7, spread=0.02)
+        cfg.box = (5.0, 5.0, 4.0)    # 3 x 3 x 2 cells of 1.43 nm
     else:
         cfg = I.ragged_batch([700, 1, 129, 2500, 40], seed=6, spread=0.03)
     if which == "bubbles":
@@ -69,12 +75,16 @@ def test_noalloc_forces_equal_the_context_path_on_two_calls(which):
         out.append((Fb.cpu().numpy(), Fp.cpu().numpy()))
     po = O.params(box=cfg.box, **kw) if cfg.box[0] > 0 else O.params(**kw)
     Sb, Sp = O.force_scale(po, cfg.n_bp, Xs, us)
-    if which == "bubbles":       # the rule removed terms here: the context path matches the oracle too
+    if which in ("bubbles", "small_box"):   # the context path matches the oracle here too
         ro = O.forces(po, cfg.n_bp, Xs, us)
         assert (np.linalg.norm(Fb_ref - ro["Fb"], axis=1) <= REL * Sb + ABS).all()
+    if which == "small_box":     # the pairs across the short edge are there
+        assert O.forces(po, cfg.n_bp, Xs, us)["energy"][:, 3].sum() > 1.0
     for Fb, Fp in out:
         assert (np.linalg.norm(Fb - Fb_ref, axis=1) <= REL * Sb + ABS).all()
         assert (np.linalg.norm(Fp - Fp_ref, axis=1) <= REL * Sp + ABS).all()
+    # the second call starts from the first call's leftovers in the shared array
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
 def test_noalloc_rejects_inputs_beyond_its_fixed_scratch():
@@ -89,3 +99,5 @@ def test_noalloc_rejects_inputs_beyond_its_fixed_scratch():
     assert _call(L, p2, [100], X, X, F, F, 0) == -1
     p3 = D.dsdna_default_params(precision=D.PREC_FP64)
     assert _call(L, p3, [100], X, X, F, F, 0) == -1
+    for bad in (dict(skin=-0.1), dict(skin=1.5), dict(bubble_rule=3), dict(steric_phase=3), dict(steric_phase=-1)):
+        assert _call(L, D.dsdna_default_params(**bad), [100], X, X, F, F, 0) == -1, bad
