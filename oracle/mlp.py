@@ -9,6 +9,15 @@ Inputs are normalised as (x - in_mean) / in_scale; the network's output o is
 mapped to y = out_mean + out_scale * o; the loss is the mean over all B x 3
 entries of (o - (t - out_mean) / out_scale)^2.  GELU is the exact form
 0.5 z (1 + erf(z / sqrt 2)).
+
+``operands="bf16"`` follows the arithmetic contract of the tensor-core
+kernels instead of exact arithmetic: each matrix contraction takes BF16
+operands (the normalised inputs, the activations H1 and H2 and the output
+gradient of the forward and backward products that run on the tensor cores,
+and dZ2) and sums them exactly, while the 3- and 4-wide gradient reductions
+(dW3 = dY^T H2, dW1 = dZ1^T Xn and the biases) take their FP32 operands as
+they are.  With the weights already rounded to BF16 it differs from the
+kernels only by their FP32 accumulation and FP32 GELU.
 """
 from __future__ import annotations
 
@@ -52,23 +61,32 @@ def bf16(x):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def forward(p, X, norm):
+def _operand(operands):
+    if operands is None:
+        return lambda a: a
+    assert operands == "bf16", operands
+    return bf16
+
+
+def forward(p, X, norm, operands=None):
     """Outputs y [B, 3] and the intermediates needed by backward."""
+    r = _operand(operands)
     w = unpack(p)
     xn = (np.asarray(X, np.float64) - norm["in_mean"]) / norm["in_scale"]
-    z1 = xn @ w["W1"].T + w["b1"]
+    z1 = r(xn) @ w["W1"].T + w["b1"]
     h1 = gelu(z1)
-    z2 = h1 @ w["W2"].T + w["b2"]
+    z2 = r(h1) @ w["W2"].T + w["b2"]
     h2 = gelu(z2)
-    o = h2 @ w["W3"].T + w["b3"]
+    o = r(h2) @ w["W3"].T + w["b3"]
     y = norm["out_mean"] + norm["out_scale"] * o
     return y, dict(xn=xn, z1=z1, h1=h1, z2=z2, h2=h2, o=o)
 
 
-def loss_and_grad(p, X, T, norm):
+def loss_and_grad(p, X, T, norm, operands=None):
     """Mean squared error on normalised outputs and its gradient (packed)."""
+    r = _operand(operands)
     w = unpack(p)
-    y, c = forward(p, X, norm)
+    y, c = forward(p, X, norm, operands)
     tn = (np.asarray(T, np.float64) - norm["out_mean"]) / norm["out_scale"]
     e = c["o"] - tn
     B = e.shape[0]
@@ -77,13 +95,24 @@ def loss_and_grad(p, X, T, norm):
     g = {}
     g["W3"] = do.T @ c["h2"]
     g["b3"] = do.sum(0)
-    dz2 = (do @ w["W3"]) * gelu_d(c["z2"])
-    g["W2"] = dz2.T @ c["h1"]
+    dz2 = (r(do) @ w["W3"]) * gelu_d(c["z2"])
+    g["W2"] = r(dz2).T @ r(c["h1"])
     g["b2"] = dz2.sum(0)
-    dz1 = (dz2 @ w["W2"]) * gelu_d(c["z1"])
+    dz1 = (r(dz2) @ w["W2"]) * gelu_d(c["z1"])
     g["W1"] = dz1.T @ c["xn"]
     g["b1"] = dz1.sum(0)
     return loss, pack(g)
+
+
+def bf16_operands(p, X, T, norm):
+    """Every value ``operands="bf16"`` rounds to BF16 (flattened), for
+    checking how far each lies from a BF16 rounding boundary."""
+    w = unpack(p)
+    _, c = forward(p, X, norm, "bf16")
+    tn = (np.asarray(T, np.float64) - norm["out_mean"]) / norm["out_scale"]
+    do = 2.0 * (c["o"] - tn) / (c["o"].shape[0] * NO)
+    dz2 = (bf16(do) @ w["W3"]) * gelu_d(c["z2"])
+    return np.concatenate([a.ravel() for a in (c["xn"], c["h1"], c["h2"], do, dz2)])
 
 
 def init_params(seed=0):

@@ -61,6 +61,37 @@ def test_bf16_rounding():
     assert abs(M.bf16(math.pi) - math.pi) < 2 ** -8 * math.pi
 
 
+def test_bf16_operand_mode_rounds_each_contraction_operand():
+    """operands="bf16" (the kernels' contract: BF16 operands, exact sums) on a
+    network wired as a chain through unit 0 -- W1 = e0 e0^T, W2 = identity,
+    W3 = e0^T, zero biases, inputs not normalised -- so its output and the
+    gradient of W2[0][0] follow in closed form from GELU and BF16 rounding:
+    o0 = bf16(gelu(bf16(gelu(bf16(x0))))) and
+    dW2[0][0] = bf16(bf16(do0) gelu'(z2_0)) bf16(h1_0), where exact arithmetic
+    has no bf16().  One row, input pi and target 0."""
+    d = M.unpack(np.zeros(M.NP))
+    d["W1"][0, 0] = 1.0
+    d["W2"] = np.eye(M.NH)
+    d["W3"][0, 0] = 1.0
+    p = M.pack(d)
+    n = dict(in_mean=np.zeros(4), in_scale=np.ones(4), out_mean=np.zeros(3), out_scale=np.ones(3))
+    X = np.array([[math.pi, 0.0, 0.0, 0.0]])
+    T = np.zeros((1, 3))
+    h1 = M.gelu(M.bf16(math.pi))
+    z2 = M.bf16(h1)
+    o0 = M.bf16(M.gelu(z2))
+    y, _ = M.forward(p, X, n, operands="bf16")
+    assert y[0, 0] == o0 and y[0, 0] != M.gelu(M.gelu(math.pi))
+    _, g = M.loss_and_grad(p, X, T, n, operands="bf16")
+    do0 = 2.0 * o0 / 3.0
+    want = M.bf16(M.bf16(do0) * M.gelu_d(z2)) * M.bf16(h1)
+    assert M.unpack(g)["W2"][0, 0] == want
+    # exact arithmetic keeps every operand
+    _, ge = M.loss_and_grad(p, X, T, n)
+    he = M.gelu(math.pi); oe = M.gelu(M.gelu(math.pi))
+    assert abs(M.unpack(ge)["W2"][0, 0] - 2.0 * oe / 3.0 * M.gelu_d(he) * he) < 1e-15
+
+
 def test_first_adam_step_has_closed_form():
     """From zero moments the bias-corrected first step is lr g / (|g| + eps),
     i.e. lr sign(g) for |g| >> eps, plus lr wd p on the weights only."""
