@@ -216,35 +216,67 @@ def random_walk_helix(n_bp: int = 3000, phi: float = 0.05, seg_bp: int = 30, max
     rng = np.random.default_rng(seed)
     L = box_edge(2 * n_bp, phi)
     nseg = (n_bp + seg_bp - 1) // seg_bp
-    # segments are filed by the cell of their middle point; a cell is wider than
-    # a segment plus the clearance, so clashes only occur with the 27 neighbour cells
-    reach = RISE * seg_bp + clearance + 0.5
-    ncell = max(1, int(L // reach))
-    h = L / ncell
-    grid: dict = {}
     maxj = math.radians(max_joint_deg)
     j = np.arange(1, seg_bp + 1)
     frac = np.minimum(j, joint_bp) / float(joint_bp)
     sample = np.arange(0, seg_bp, 3)
     c2 = clearance * clearance
-    offs = [(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)]
+    # sample points are filed in a grid of cells at least `clearance` wide (KS
+    # slots per cell, a dict for the rare overflow), so every earlier point
+    # closer than the clearance sits in one of the 27 cells around a new point
+    nc = max(1, int(L // clearance))
+    hc = L / nc
+    KS = 6
+    seg_of = np.full((nc ** 3, KS), -1, np.int32)
+    spts = np.zeros((nc ** 3, KS, 3))
+    spill: dict = {}
+    offs = np.array([(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)])
 
-    def cell_of(q):
-        w = np.floor((q % L) / h).astype(int) % ncell
-        return (int(w[0]), int(w[1]), int(w[2]))
+    def cells_of(q):
+        w = np.floor((q % L) / hc).astype(np.int64) % nc
+        return (w[:, 0] * nc + w[:, 1]) * nc + w[:, 2]
+
+    def around(q):
+        w = np.floor((q % L) / hc).astype(np.int64) % nc
+        v = (w[:, None, :] + offs[None, :, :]) % nc
+        return (v[..., 0] * nc + v[..., 1]) * nc + v[..., 2]        # [points, 27]
 
     def clash(pts, s):
-        w = cell_of(pts[len(pts) // 2])
-        keys = {((w[0] + a) % ncell, (w[1] + b) % ncell, (w[2] + c) % ncell) for a, b, c in offs}
-        cand = [e[1] for k in keys for e in grid.get(k, ()) if e[0] < s - 2]
-        if not cand:
-            return False
-        Q = np.concatenate(cand)
-        d = pts[:, None, :] - Q[None, :, :]
-        d -= L * np.round(d / L)
-        return bool(((d * d).sum(-1) < c2).any())
+        idx = around(pts)
+        sg = seg_of[idx]                                             # [points, 27, KS]
+        ok = (sg >= 0) & (sg < s - 2)
+        if ok.any():
+            d = pts[:, None, None, :] - spts[idx]
+            d -= L * np.round(d / L)
+            if (((d * d).sum(-1) < c2) & ok).any():
+                return True
+        if spill:
+            for i, q in enumerate(pts):
+                for c in set(idx[i].tolist()):
+                    for e, qq in spill.get(c, ()):
+                        if e < s - 2:
+                            dd = q - qq
+                            dd -= L * np.round(dd / L)
+                            if dd @ dd < c2:
+                                return True
+        return False
 
-    segs = []          # accepted segments: (pts, ts, ns, sample cells)
+    def file(pts, s):
+        for c, q in zip(cells_of(pts).tolist(), pts):
+            free = np.flatnonzero(seg_of[c] < 0)
+            if len(free):
+                seg_of[c, free[0]] = s
+                spts[c, free[0]] = q
+            else:
+                spill.setdefault(c, []).append((s, q))
+
+    def unfile(pts, s):
+        for c in cells_of(pts).tolist():
+            seg_of[c][seg_of[c] == s] = -1
+            if c in spill:
+                spill[c] = [e for e in spill[c] if e[0] != s]
+
+    segs = []          # accepted segments: (pts, ts, ns)
     t0 = np.array([0.0, 0.0, 1.0]); n0 = np.array([1.0, 0.0, 0.0])
     start = rng.uniform(0, L, size=3) - RISE * t0
     fails = 0
@@ -270,18 +302,16 @@ def random_walk_helix(n_bp: int = 3000, phi: float = 0.05, seg_bp: int = 30, max
                 placed = True
                 break
         if placed:
-            w = cell_of(pts[sample][len(sample) // 2])
-            segs.append((pts, ts, ns, w))
-            grid.setdefault(w, []).append((s, pts[sample]))
+            segs.append((pts, ts, ns))
+            file(pts[sample], s)
             continue
         fails += 1
         if fails > 20 * nseg + 1000:
             raise RuntimeError("could not grow the self-avoiding helix")
         back = min(len(segs), 1 + int(rng.integers(0, 4)))
         for _ in range(back):
-            _, _, _, w = segs.pop()
-            sdrop = len(segs)
-            grid[w] = [e for e in grid[w] if e[0] != sdrop]
+            pts_d, _, _ = segs.pop()
+            unfile(pts_d[sample], len(segs))
     axis = np.concatenate([sg[0] for sg in segs])[:n_bp]
     T = np.concatenate([sg[1] for sg in segs])[:n_bp]
     Nn = np.concatenate([sg[2] for sg in segs])[:n_bp]
@@ -384,26 +414,59 @@ def c3_confined(n_bp: int = 1_000_000, phi: float = 0.05, seed: int = 0) -> Conf
     return cfg
 
 
-def c4_batch(n_mol: int = 256, lo: int = 500, hi: int = 20_000, seed: int = 0) -> Config:
+def c3_walk(n_bp: int = 1_000_000, phi: float = 0.05, seed: int = 0) -> Config:
+    """One dsDNA molecule confined in a periodic cube at volume fraction phi,
+    grown as a self-avoiding walk of straight 30 bp helical segments joined at
+    angles of at most 30 degrees (each joint spread over 5 base pairs), with
+    the helical phase continuous along the chain and axis points of
+    non-adjacent segments at least 2.2 nm apart (periodic distance); random
+    sequence (force-inert).  Coordinates stay unwrapped."""
+    cfg = random_walk_helix(n_bp=n_bp, phi=phi, seg_bp=30, max_joint_deg=30.0, clearance=2.2, joint_bp=5, seed=seed)
+    cfg.name = "confined_walk_%dbp_phi%.2f" % (n_bp, phi)
+    return cfg
+
+
+def random_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniformly distributed rotation matrix (normalised Gaussian quaternion)."""
+    q = rng.normal(size=4)
+    a, b, c, d = q / np.linalg.norm(q)
+    return np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                     [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                     [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+
+
+def c4_batch(n_mol: int = 256, lo: int = 500, hi: int = 20_000, seed: int = 0, random_pose: bool = False,
+             spread: float = 200.0) -> Config:
     """Independent linear molecules, lengths log-uniform in [lo, hi] bp, each
-    anchored at bp 0 and loaded with its own force (U[0.1, 10] e_z) and torque
-    (U[-5, 5] e_z) on the last base pair."""
+    anchored at bp 0 and loaded with its own force (U[0.1, 10] along the
+    molecule's axis) and torque (U[-5, 5] about it) on the last base pair.
+    Molecules are relaxed straight helices along +z from the origin, or with
+    random_pose each turned by a uniformly random rotation about its first
+    base pair and moved to a uniformly random origin in a cube of edge
+    `spread` nm (its load turned with it)."""
     rng = np.random.default_rng(seed)
     n_bp = np.exp(rng.uniform(math.log(lo), math.log(hi), size=n_mol)).astype(np.int32)
     n_bp = np.clip(n_bp, lo, hi).astype(np.int32)
-    Xs, us = [], []
+    pose = np.random.default_rng(seed + 7919) if random_pose else None
+    Xs, us, R = [], [], []
     for nb in n_bp:
         X, u = straight_helix(int(nb))
-        Xs.append(X); us.append(u)
+        Rm = np.eye(3)
+        if pose is not None:
+            Rm = random_rotation(pose)
+            X = X @ Rm.T + pose.uniform(-0.5 * spread, 0.5 * spread, size=3)
+            u = u @ Rm.T
+        Xs.append(X); us.append(u); R.append(Rm)
     X = np.concatenate(Xs); u = np.concatenate(us)
     tether = np.ones(n_mol, np.int32)
     V, Om = maxwell(u, rng, frozen=_frozen_mask(n_bp, tether))
     f = rng.uniform(0.1, 10.0, size=n_mol)
     g = rng.uniform(-5.0, 5.0, size=n_mol)
-    ext_f = np.zeros((n_mol, 3)); ext_f[:, 2] = f
-    ext_t = np.zeros((n_mol, 3)); ext_t[:, 2] = g
-    return Config("batch_%dx[%d,%d]bp" % (n_mol, lo, hi), n_bp, X, u, V, Om, tether=tether,
-                  ext_f=ext_f, ext_t=ext_t)
+    R = np.asarray(R)
+    ext_f = f[:, None] * R[:, :, 2]     # the molecule's own axis (z before the turn)
+    ext_t = g[:, None] * R[:, :, 2]
+    name = "batch_%dx[%d,%d]bp%s" % (n_mol, lo, hi, "_random_pose" if random_pose else "")
+    return Config(name, n_bp, X, u, V, Om, tether=tether, ext_f=ext_f, ext_t=ext_t)
 
 
 def paper_array(nx: int = 40, ny: int = 40, n_bp: int = 600, spacing: float = 5.0, seed: int = 0) -> Config:
