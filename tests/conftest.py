@@ -1,3 +1,4 @@
+import functools
 import os
 import sys
 
@@ -24,3 +25,11 @@ def read_golden(name):
             k, v = line.split("=", 1)
             out[k.strip()] = v.strip()
     return out
+
+
+@functools.lru_cache(maxsize=1)
+def c3_walk():
+    """The 1 Mbp confined self-avoiding walk of the throughput benchmark,
+    built once per test session (about a minute of host time)."""
+    from paper_1608_03722_gb300 import inputs as I
+    return I.c3_walk()

@@ -16,6 +16,7 @@ import pytest
 import oracle as O
 from paper_1608_03722_gb300 import dsdna as D
 from paper_1608_03722_gb300 import inputs as I
+from tests.conftest import c3_walk
 
 pytestmark = pytest.mark.gpu
 
@@ -107,6 +108,17 @@ def test_forces_periodic_dense(prec):
 def test_forces_with_applied_load(prec):
     cfg = I.c4_batch(n_mol=5, lo=20, hi=300, seed=2)
     rng = np.random.default_rng(4)
+    cfg.X, cfg.u = I.perturb(cfg.X, cfg.u, rng, dx=0.02, dtheta=0.05)
+    check_forces(cfg, prec, ext=True)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_forces_with_applied_load_random_poses(prec):
+    """Molecules turned in random directions and placed anywhere in an open
+    box (hashed cell table off its favourable axis), each loaded along its
+    own axis."""
+    cfg = I.c4_batch(n_mol=6, lo=20, hi=400, seed=5, random_pose=True, spread=30.0)
+    rng = np.random.default_rng(6)
     cfg.X, cfg.u = I.perturb(cfg.X, cfg.u, rng, dx=0.02, dtheta=0.05)
     check_forces(cfg, prec, ext=True)
 
@@ -306,10 +318,12 @@ def test_library_builds_default_helix_like_oracle():
     ctx.close()
 
 
-def test_c3_full_size_sampled_forces():
-    """The 1 Mbp confined helix (2e6 nucleotides) of the throughput benchmark, at its
-    launch configuration, on a sample of nucleotides the oracle evaluates one by one."""
-    cfg = I.c3_confined()
+@pytest.mark.parametrize("layout", ["walk", "rows"])
+def test_c3_full_size_sampled_forces(layout):
+    """The 1 Mbp confined helix (2e6 nucleotides) of the throughput benchmark
+    (the self-avoiding walk; also the rows-and-U-turns layout), at its launch
+    configuration, on a sample of nucleotides the oracle evaluates one by one."""
+    cfg = c3_walk() if layout == "walk" else I.c3_confined()
     ctx = ctx_for(cfg, D.PREC_MIXED)
     Fb, Fp = ctx.compute_forces()
     Xs, _, us, _ = ctx.get_state()
