@@ -52,9 +52,14 @@ def max_over_ranks(dist, x: float, device) -> float:
 def build_workload(name: str, seed: int = 0, n_bp: int = 1_000_000):
     from paper_1608_03722_gb300 import inputs as I
     if name == "c3":
+        cfg = I.c3_walk(n_bp=n_bp, seed=seed)
+        desc = (f"confined self-avoiding dsDNA, {n_bp:,} bp = {2 * n_bp:,} nucleotides, self-avoiding walk of "
+                f"30 bp helical segments (joints <= 30 deg) in a periodic cube L={cfg.box[0]:.2f} nm "
+                f"(volume fraction 0.05), Langevin kT=1, dt=0.005")
+    elif name == "c3rows":
         cfg = I.c3_confined(n_bp=n_bp, seed=seed)
-        desc = (f"confined self-avoiding dsDNA, {n_bp:,} bp = {2 * n_bp:,} nucleotides, periodic cube "
-                f"L={cfg.box[0]:.2f} nm (volume fraction 0.05), Langevin kT=1, dt=0.005")
+        desc = (f"confined self-avoiding dsDNA, {n_bp:,} bp = {2 * n_bp:,} nucleotides, rows along x joined by "
+                f"U-turns in a periodic cube L={cfg.box[0]:.2f} nm (volume fraction 0.05), Langevin kT=1, dt=0.005")
     elif name == "c2":
         cfg = I.c2_tethered(force=5.0, torque=2.0, seed=seed)
         desc = "tethered linear dsDNA, 10 kbp = 20,000 nucleotides, f=5 kT/nm, torque 2 kT"
@@ -76,7 +81,7 @@ def build_workload(name: str, seed: int = 0, n_bp: int = 1_000_000):
 # kernel from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
 # the bench's multi-step launches on the 1 Mbp confined workload), keyed by a
 # hash of the kernel sources it was taken on: a changed kernel reports no traffic.
-ENGINE_TRAFFIC = {"dca68512036919e4": 211.9}   # 1 Mbp confined workload, skin 0.3
+ENGINE_TRAFFIC = {("dca68512036919e4", "c3rows"): 211.9}   # 1 Mbp confined rows, skin 0.3
 ENGINE_SOURCES = ("engine.cuh", "engine_kernels.cuh", "kern_mixed.cu")   # the step kernel's code
 
 
@@ -89,11 +94,11 @@ def engine_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def engine_traffic_per_nt_step(prec):
+def engine_traffic_per_nt_step(prec, workload):
     from paper_1608_03722_gb300 import dsdna as D
     if prec != D.PREC_MIXED:
         return None
-    return ENGINE_TRAFFIC.get(engine_source_hash())
+    return ENGINE_TRAFFIC.get((engine_source_hash(), workload))
 
 
 def peaks():
@@ -171,21 +176,84 @@ def gpu_uuid(torch, dev):
         return None
 
 
-def run_cpu_oracle(cfg, steps: int, seconds_cap: float = 25.0):
-    """Time the FP64 oracle (as it stands, cell-hash pair search) on whole Langevin steps of the workload."""
+def run_cpu_oracle(cfg, steps: int, seconds_cap: float = 25.0, chunk: int = 1, seed: int = 0):
+    """Time the FP64 oracle (as it stands, cell-hash pair search) on whole
+    Langevin steps of the workload, `chunk` steps per call, one thread."""
     import oracle as O
-    p = O.params(box=cfg.box) if cfg.box[0] > 0 else O.params()
+    p = O.params(box=cfg.box, seed=seed) if cfg.box[0] > 0 else O.params(seed=seed)
     X, V, u, Om = (a.copy() for a in (cfg.X, cfg.V, cfg.u, cfg.Om))
     done = 0
     t0 = time.perf_counter()
+    w0 = time.time()
     while done < steps:
-        O.run(p, cfg.n_bp, X, V, u, Om, 1, step0=done, ext_f=cfg.ext_f, ext_t=cfg.ext_t, tether=cfg.tether,
+        n = min(chunk, steps - done)
+        O.run(p, cfg.n_bp, X, V, u, Om, n, step0=done, ext_f=cfg.ext_f, ext_t=cfg.ext_t, tether=cfg.tether,
               cells=True)
-        done += 1
+        done += n
         if time.perf_counter() - t0 > seconds_cap:
             break
     dt = time.perf_counter() - t0
-    return cfg.n_nt * done / dt, done, dt
+    return cfg.n_nt * done / dt, done, dt, (w0, time.time())
+
+
+def _oracle_worker(job):
+    """One independent replica of the workload on one host core (spawned process)."""
+    path, seed, steps, cap, chunk = job
+    sys.path.insert(0, ROOT)
+    from paper_1608_03722_gb300 import inputs as I
+    d = np.load(path)
+    opt = lambda k: d[k] if d[k].size else None
+    cfg = I.Config("replica", d["n_bp"], d["X"], d["u"], d["V"], d["Om"], box=tuple(d["box"]), tether=opt("tether"),
+                   ext_f=opt("ext_f"), ext_t=opt("ext_t"))
+    _, done, _, (w0, w1) = run_cpu_oracle(cfg, steps, cap, chunk, seed)
+    return cfg.n_nt * done, w0, w1
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_cpu_oracle_all_cores(cfg, steps: int, seconds_cap: float, chunk: int = 1, workers: int | None = None):
+    """The oracle as it stands on every host core: one independent replica of
+    the workload per core (its own noise seed), started together in spawned
+    processes; nucleotide-steps of all replicas over the span from the first
+    start to the last finish."""
+    import multiprocessing as mp
+    workers = workers or host_cores()
+    none = np.zeros(0)
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "cfg.npz")
+        np.savez(path, n_bp=cfg.n_bp, X=cfg.X, u=cfg.u, V=cfg.V, Om=cfg.Om, box=np.asarray(cfg.box, float),
+                 tether=none if cfg.tether is None else cfg.tether, ext_f=none if cfg.ext_f is None else cfg.ext_f,
+                 ext_t=none if cfg.ext_t is None else cfg.ext_t)
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.map(_oracle_worker, [(path, 1000 + r, steps, seconds_cap, chunk) for r in range(workers)])
+    total = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    return total / span, total, span, workers
+
+
+def cpu_baseline(cfg, c3_steps=2, c3_cap=20.0, c1_steps=10_000):
+    """The oracle on the host: the bench's workload (whole steps, one thread and
+    all cores) and the 200 bp molecule for its full 10^4 steps."""
+    from paper_1608_03722_gb300 import inputs as I
+    cores = host_cores()
+    v1, done, dt, _ = run_cpu_oracle(cfg, c3_steps, c3_cap)
+    va, tot, span, w = run_cpu_oracle_all_cores(cfg, c3_steps, c3_cap)
+    c1 = I.c1_linear(200)
+    u1, d1, t1, _ = run_cpu_oracle(c1, c1_steps, 120.0, chunk=500)
+    ua, tot1, span1, _ = run_cpu_oracle_all_cores(c1, c1_steps, 120.0, chunk=500)
+    return {"value": va, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{c3_steps} whole Langevin steps of the full workload ({cfg.n_nt} nucleotides) on each of "
+                      f"{w} cores, one independent replica per core ({span:.1f} s)",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"{done} whole Langevin steps of the full workload, {dt:.1f} s"},
+            "c1_200bp_1e4_steps": {"single_thread": {"value": u1, "unit": UNIT, "steps": d1, "seconds": t1},
+                                   "all_cores": {"value": ua, "unit": UNIT, "cores": w, "seconds": span1,
+                                                 "sample": f"{c1_steps} steps of 200 bp on each core"}}}
 
 
 def timed_steps(ctx, torch, steps, reps):
@@ -202,37 +270,63 @@ def timed_steps(ctx, torch, steps, reps):
     return e0.elapsed_time(e1) * 1e-3
 
 
-def compare_batched(D, torch, n_mol=256, steps=100, fp64_sample=16, fp64_steps=50):
-    """Batched mixed-precision engine (256 ragged molecules, one graph-driven
-    persistent launch, autotuned) against the plain FP64 path that runs one
-    molecule per context, on the same molecules (FP64 timed on a sample)."""
+def _batch_rate(D, torch, cfg, p, steps, reps):
+    ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether)
+    for m in range(len(cfg.n_bp)):
+        ctx.set_external_force_torque(m, cfg.ext_f[m], cfg.ext_t[m])
+    t = timed_steps(ctx, torch, steps, reps)
+    ctx.close()
+    return cfg.n_nt * steps * reps / t
+
+
+def _per_molecule_rate(D, torch, cfg, prec, steps):
+    """Every molecule in a context of its own (default launch parameters),
+    run one after the other: nucleotide-steps over the summed device time."""
+    off = np.concatenate([[0], np.cumsum(cfg.n_bp)])
+    nt_steps, secs = 0, 0.0
+    for m in range(len(cfg.n_bp)):
+        sl = slice(2 * off[m], 2 * off[m + 1])
+        c1 = D.Context(D.dsdna_default_params(precision=prec), [int(cfg.n_bp[m])], X=cfg.X[sl], V=cfg.V[sl],
+                       u=cfg.u[sl], Om=cfg.Om[sl], tether=[1])
+        c1.set_external_force_torque(0, cfg.ext_f[m], cfg.ext_t[m])
+        secs += timed_steps(c1, torch, steps, 1)
+        nt_steps += 2 * int(cfg.n_bp[m]) * steps
+        c1.close()
+    return nt_steps / secs
+
+
+def compare_batched(D, torch, n_mol=256, steps=100):
+    """C4, 256 ragged tethered molecules with their own loads, four ways on
+    the same molecules: batched (one context, one graph-driven persistent
+    launch, autotuned) or one molecule per context, each in mixed precision
+    and in FP64, so the gain splits into its batching and precision parts;
+    and the batched mixed run with the molecules in random orientations and
+    places."""
     from paper_1608_03722_gb300 import inputs as I
     cfg = I.c4_batch(n_mol=n_mol, seed=0)
-    p = D.dsdna_default_params()
-    p, _ = D.dsdna_autotune(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether, trial_steps=30)
-    ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether)
-    for m in range(n_mol):
-        ctx.set_external_force_torque(m, cfg.ext_f[m], cfg.ext_t[m])
-    t = timed_steps(ctx, torch, steps, 3)
-    batched = cfg.n_nt * steps * 3 / t
-    ctx.close()
-    off = np.concatenate([[0], np.cumsum(cfg.n_bp)])
-    rng = np.random.default_rng(1)
-    sample = np.sort(rng.choice(n_mol, size=fp64_sample, replace=False))
-    nt_steps, secs = 0, 0.0
-    for m in sample:
-        sl = slice(2 * off[m], 2 * off[m + 1])
-        pm = D.dsdna_default_params(precision=D.PREC_FP64)
-        c1 = D.Context(pm, [int(cfg.n_bp[m])], X=cfg.X[sl], V=cfg.V[sl], u=cfg.u[sl], Om=cfg.Om[sl], tether=[1])
-        c1.set_external_force_torque(0, cfg.ext_f[m], cfg.ext_t[m])
-        secs += timed_steps(c1, torch, fp64_steps, 1)
-        nt_steps += 2 * int(cfg.n_bp[m]) * fp64_steps
-        c1.close()
-    fp64 = nt_steps / secs
-    return {"workload": f"{n_mol} molecules log-uniform 500-20000 bp ({cfg.n_nt} nucleotides), own force and torque each",
-            "batched_mixed": {"value": batched, "unit": UNIT, "skin": p.skin, "block_threads": p.block_threads},
-            "fp64_per_molecule": {"value": fp64, "unit": UNIT, "sample_molecules": int(fp64_sample)},
-            "speedup": batched / fp64}
+    out = {"workload": f"{n_mol} tethered molecules log-uniform 500-20000 bp ({cfg.n_nt} nucleotides), own force "
+                       f"and torque each, {steps}-step runs"}
+    for name, prec in (("mixed", D.PREC_MIXED), ("fp64", D.PREC_FP64)):
+        p, _ = D.dsdna_autotune(D.dsdna_default_params(precision=prec), cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om,
+                                tether=cfg.tether, trial_steps=30)
+        out["batched_" + name] = {"value": _batch_rate(D, torch, cfg, p, steps, 3), "unit": UNIT, "skin": p.skin,
+                                  "block_threads": p.block_threads}
+        out["per_molecule_" + name] = {"value": _per_molecule_rate(D, torch, cfg, prec, steps), "unit": UNIT,
+                                       "molecules": n_mol}
+    b = {k: out[k]["value"] for k in ("batched_mixed", "batched_fp64", "per_molecule_mixed", "per_molecule_fp64")}
+    out["speedup"] = b["batched_mixed"] / b["per_molecule_fp64"]
+    out["batching_gain_mixed"] = b["batched_mixed"] / b["per_molecule_mixed"]
+    out["batching_gain_fp64"] = b["batched_fp64"] / b["per_molecule_fp64"]
+    out["precision_gain_batched"] = b["batched_mixed"] / b["batched_fp64"]
+    out["precision_gain_per_molecule"] = b["per_molecule_mixed"] / b["per_molecule_fp64"]
+    rp = I.c4_batch(n_mol=n_mol, seed=0, random_pose=True)
+    p, _ = D.dsdna_autotune(D.dsdna_default_params(), rp.n_bp, X=rp.X, V=rp.V, u=rp.u, Om=rp.Om, tether=rp.tether,
+                            trial_steps=30)
+    out["batched_mixed_random_pose"] = {"value": _batch_rate(D, torch, rp, p, steps, 3), "unit": UNIT,
+                                        "skin": p.skin, "block_threads": p.block_threads,
+                                        "pose": "uniformly random rotation about base pair 0, origin uniform in a "
+                                                "200 nm cube, load along the molecule's own axis"}
+    return out
 
 
 # Paper's time unit: tau_Br = 2.28e-9 s and dt = 0.005 tau_Br (App. A), so
@@ -302,14 +396,18 @@ def reference_arm(args, ws, rank):
     cfg, desc = build_workload(args.workload, n_bp=args.n_bp)
     import oracle as O
     O.build()
-    value, done, dt = run_cpu_oracle(cfg, args.steps, seconds_cap=max(30.0, 20.0 * args.steps))
+    # every host core runs an independent replica of the workload; a bench step is
+    # one whole Langevin step of every replica
+    value, total, span, cores = run_cpu_oracle_all_cores(cfg, args.steps, seconds_cap=max(30.0, 20.0 * args.steps))
+    done = int(round(total / cfg.n_nt / cores))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": done,
-        "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(done, 1), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1e3 * span / max(done, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "md_steps_per_step": 1, "l2": "state larger than L2"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{done} whole Langevin steps of the full workload ({cfg.n_nt} nucleotides)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{done} whole Langevin steps of the full workload ({cfg.n_nt} nucleotides) on each "
+                                   f"of {cores} cores, one independent replica per core"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -322,7 +420,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "paper960"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c3rows", "c4", "paper960"])
     ap.add_argument("--md-steps", type=int, default=100)
     ap.add_argument("--n-bp", type=int, default=1_000_000, help="base pairs of the confined workload")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -431,7 +529,7 @@ def main():
     launch_s = prof["engine_ms"] * 1e-3 / max(prof["engine_launches"], 1)
     hbm, peak_kind = peaks()
     achieved = per_launch_bytes / launch_s / 1e9
-    traffic = engine_traffic_per_nt_step(prec)
+    traffic = engine_traffic_per_nt_step(prec, args.workload)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": None if traffic is None else traffic * cfg.n_nt * steps_per_launch,
             "peak_kind": peak_kind, "bytes_per_nt_step": b_nt, "neighbors_per_bead": nbar,
@@ -462,10 +560,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, done, dt = run_cpu_oracle(cfg, 3, seconds_cap=25.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{done} whole Langevin step(s) of the full workload ({cfg.n_nt} nucleotides), "
-                         f"{dt:.1f} s, single thread"}
+        cpu = cpu_baseline(cfg)
 
     compare = None
     if rank == 0 and not args.no_compare:
@@ -473,18 +568,31 @@ def main():
         compare["paper_benchmark"] = compare_paper(D, torch)
         compare["supercoiled_ring"] = compare_ring(D, torch)
         from paper_1608_03722_gb300 import surrogate as SUR
-        st = SUR.run_sweep_study(n_train=256, n_test=64, n_query=32, length=(100, 400), steps=8000,
-                                 measure_from=2000, every=100, iters=3000)
+        t_s = time.perf_counter()
+        st = SUR.run_sweep_study(n_train=2000, n_test=200, n_query=100, length=(500, 20000), steps=8000,
+                                 measure_from=2000, every=200, iters=3000, query_rounds=3)
         compare["surrogate"] = {
-            "workload": "sweep of tethered molecules 100-400 bp, force 0.1-10 kT/nm, torque -5..5 kT, kT 0.8-1.4 "
-                        "(256 training / 64 held-out points, 8000 steps each)",
+            "workload": "sweep of tethered molecules 500-20000 bp, force 0.1-10 kT/nm, torque -5..5 kT, kT 0.8-1.4 "
+                        "(2000 training / 200 held-out points, 8000 steps each; 3 rounds of 100 committee-picked "
+                        "against 100 random additions)",
             "held_out_r2": st["held_out"]["r2"], "held_out_rmse": st["held_out"]["rmse"],
             "replicate_noise": st["replicate_noise"],
             "rmse_over_replicate_noise": st["held_out"]["rmse_over_replicate_noise"],
+            "dropped_points": st["dropped_points"],
             "simulation_s_per_point": st["simulation_s_per_point"],
             "surrogate_s_per_point": st["surrogate_s_per_point"], "speedup_per_point": st["speedup_per_point"],
-            "r2_after_committee_queries": st["after_committee_queries"]["r2"],
-            "r2_after_random_queries": st["after_random_queries"]["r2"]}
+            "r2_after_committee_queries": [r["committee"]["r2"] for r in st["query_rounds"]],
+            "r2_after_random_queries": [r["random"]["r2"] for r in st["query_rounds"]],
+            "committee_minus_random_r2": st["committee_minus_random_r2"],
+            "seconds": time.perf_counter() - t_s}
+        rows_cfg, rows_desc = build_workload("c3rows", n_bp=args.n_bp)
+        pr_, _ = D.dsdna_autotune(D.dsdna_default_params(box=rows_cfg.box), rows_cfg.n_bp, X=rows_cfg.X, V=rows_cfg.V,
+                                  u=rows_cfg.u, Om=rows_cfg.Om, trial_steps=30)
+        rc_ = D.Context(pr_, rows_cfg.n_bp, X=rows_cfg.X, V=rows_cfg.V, u=rows_cfg.u, Om=rows_cfg.Om)
+        t_r = timed_steps(rc_, torch, S, 3)
+        rc_.close()
+        compare["confined_rows"] = {"workload": rows_desc, "value": rows_cfg.n_nt * S * 3 / t_r, "unit": UNIT,
+                                    "skin": pr_.skin, "block_threads": pr_.block_threads}
 
     if rank == 0:
         line = {

@@ -361,13 +361,15 @@ def _metrics(Y, T):
 
 def run_sweep_study(n_train: int = 2000, n_test: int = 200, n_query: int = 100, length=(500, 20000),
                     steps: int = 8000, measure_from: int = 2000, every: int = 200, models: int = 4,
-                    iters: int = 3000, seed: int = 0) -> dict:
+                    iters: int = 3000, seed: int = 0, query_rounds: int = 1) -> dict:
     """Train on n_train simulated sweep points, evaluate on n_test held-out
     simulated points; then add n_query points chosen by the committee or at
-    random and compare the held-out error of the two retrained surrogates.
-    The held-out points are simulated a second time with another seed: the
-    RMS difference / sqrt(2) is the sampling noise of one simulated label, the
-    yardstick for the surrogate's error."""
+    random and compare the held-out error of the two retrained surrogates
+    (query_rounds times, each with its own candidate pool, random pick and
+    initial weights, for the spread of the difference).  The held-out points
+    are simulated a second time with another seed: the RMS difference /
+    sqrt(2) is the sampling noise of one simulated label, the yardstick for
+    the surrogate's error."""
     import time
     import torch
 
@@ -395,23 +397,35 @@ def run_sweep_study(n_train: int = 2000, n_test: int = 200, n_query: int = 100, 
     base = _metrics(Y, Ttest)
     base["rmse_over_replicate_noise"] = (np.asarray(base["rmse"]) / np.maximum(rep_noise, 1e-30)).tolist()
     # query by committee vs random additions of the same size
-    cand = sample_points(20 * n_query, seed + 2, length)
-    pick = sur.select(cand, n_query)
-    rnd = np.random.default_rng(seed + 3).choice(len(cand), n_query, replace=False)
-    Tq, _ = sim(cand[pick], seed + 4)
-    Tr, _ = sim(cand[rnd], seed + 5)
-    sur.fit(np.concatenate([train, cand[pick]]), np.concatenate([Ttrain, Tq]), iters=iters)
-    qbc = _metrics(sur.predict(test)[0], Ttest)
-    sur.fit(np.concatenate([train, cand[rnd]]), np.concatenate([Ttrain, Tr]), iters=iters)
-    random_add = _metrics(sur.predict(test)[0], Ttest)
+    rounds = []
+    for q in range(query_rounds):
+        sq = seed + 100 * q
+        if q:
+            sur.close()
+            sur = Surrogate(models, max_batch=max(4096, n_train + n_query), seed=sq)
+            sur.fit(train, Ttrain, iters=iters)
+        cand = sample_points(20 * n_query, sq + 2, length)
+        pick = sur.select(cand, n_query)
+        rnd = np.random.default_rng(sq + 3).choice(len(cand), n_query, replace=False)
+        Tq, _ = sim(cand[pick], sq + 4)
+        Tr, _ = sim(cand[rnd], sq + 5)
+        sur.fit(np.concatenate([train, cand[pick]]), np.concatenate([Ttrain, Tq]), iters=iters)
+        qbc = _metrics(sur.predict(test)[0], Ttest)
+        sur.fit(np.concatenate([train, cand[rnd]]), np.concatenate([Ttrain, Tr]), iters=iters)
+        random_add = _metrics(sur.predict(test)[0], Ttest)
+        rounds.append({"committee": qbc, "random": random_add})
     sur.close()
+    gain = np.array([np.asarray(r["committee"]["r2"]) - np.asarray(r["random"]["r2"]) for r in rounds])
     return {
         "train_points": n_train, "test_points": n_test, "lengths_bp": list(length), "steps": steps,
         "outputs": ["extension/contour", "excess twist (Tw-Tw0)/Tw0", "denatured fraction"],
         "label_spread": np.nanstd(Ttest, 0).tolist(), "replicate_noise": rep_noise.tolist(),
         "dropped_points": {"train": int((~np.isfinite(Ttrain).all(1)).sum()),
                            "test": int((~np.isfinite(Ttest).all(1)).sum())},
-        "held_out": base, "after_committee_queries": qbc, "after_random_queries": random_add,
+        "held_out": base, "after_committee_queries": rounds[0]["committee"],
+        "after_random_queries": rounds[0]["random"], "query_rounds": rounds,
+        "committee_minus_random_r2": {"mean": gain.mean(0).tolist(),
+                                      "std": (gain.std(0, ddof=1) if len(gain) > 1 else np.zeros(NO)).tolist()},
         "seconds": {"simulate_train": t_train, "simulate_test": t_test, "fit": t_fit, "predict_test": t_pred},
         "simulation_s_per_point": t_test / n_test, "surrogate_s_per_point": t_pred / n_test,
         "speedup_per_point": (t_test / n_test) / max(t_pred / n_test, 1e-12),
