@@ -99,14 +99,14 @@ def test_c3_full_size_fp64_steps_match_oracle():
 
 def test_tethered_10kbp_first_thousand_steps():
     """Tethered 10 kbp molecule, f = 5 kT/nm, torque 2 kT: the mixed engine
-    against the FP64 oracle on the first 10^3 steps (same noise).  Within
-    1e-4 nm up to step 200; the divergence that follows grows
-    exponentially (chaos) and stays below 0.05 nm at step 1000."""
+    against the FP64 oracle on the first 10^3 steps (same noise).  The
+    largest centre difference grows slowly (about 2e-5 nm at step 1000) and
+    stays within 1e-4 nm over all 10^3 steps: no chaotic divergence yet."""
     cfg = I.c2_tethered(n_bp=10_000, force=5.0, torque=2.0, seed=0)
     rows, info, (X, _, _, _) = run_both(cfg, D.PREC_MIXED, 21, [100] * 10, tether=cfg.tether)
     _show("mixed tethered 10 kbp", rows)
-    assert rows[1][1] < 1e-4, rows
-    assert rows[-1][1] < 5e-2, rows
+    assert max(r[1] for r in rows) < 1e-4, rows
+    assert max(r[3] for r in rows) < 1e-3, rows
 
 
 def _quantities(cfg, prec, X, u):
@@ -133,12 +133,13 @@ def test_mixed_precision_error_per_quantity(which):
     * after 100 same-noise steps: X, V, u and Omega.
     """
     if which == "open_200bp":
-        cfg = I.c1_linear(200)
+        cfg = I.c1_linear(200)            # the trajectory starts from the relaxed helix
         rng = np.random.default_rng(31)
-        cfg.X, cfg.u = I.perturb(cfg.X, cfg.u, rng, dx=0.03, dtheta=0.06)
+        Xp, up = I.perturb(cfg.X, cfg.u, rng, dx=0.03, dtheta=0.06)   # a thermal-like configuration
     else:
         cfg = dense_walk(1200, seed=33)
-    Fb, Fp, E, W, obs, Xs, us = _quantities(cfg, D.PREC_MIXED, cfg.X, cfg.u)
+        Xp, up = cfg.X, cfg.u
+    Fb, Fp, E, W, obs, Xs, us = _quantities(cfg, D.PREC_MIXED, Xp, up)
     po = O.params(box=cfg.box) if cfg.box[0] > 0 else O.params()
     r = O.forces(po, cfg.n_bp, Xs, us)
     F = np.concatenate([r["Fb"], r["Fp"]])
