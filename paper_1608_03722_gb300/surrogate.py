@@ -432,9 +432,36 @@ def run_sweep_study(n_train: int = 2000, n_test: int = 200, n_query: int = 100, 
     }
 
 
+def kernel_passes(rows: int = 4096, passes: int = 3, seed: int = 0) -> float:
+    """`passes` training iterations (forward, backward, Adam) of one network on
+    `rows` random sweep points: a short run of the tensor-core kernels alone,
+    e.g. for a profiler.  Returns the last loss."""
+    import torch
+    pts = sample_points(rows, seed)
+    lab = np.stack([1.0 - 0.5 / np.sqrt(pts[:, 0] + 0.5), 0.01 * pts[:, 1], 0.05 * np.exp(-pts[:, 0] / 3)], 1)
+    net = Mlp(max_batch=rows)
+    m, sc = input_norm(pts)
+    net.set_params(_he_init(seed), m, sc, lab.mean(0), lab.std(0) + 1e-6)
+    X = torch.tensor(pts, dtype=torch.float32, device="cuda")
+    T = torch.tensor(lab, dtype=torch.float32, device="cuda")
+    Y = torch.empty((rows, NO), dtype=torch.float32, device="cuda")
+    loss = float("nan")
+    for _ in range(passes):
+        net.forward(X, Y)
+        loss = net.backward(T)
+        net.adam(lr=1e-3)
+    torch.cuda.synchronize()
+    net.close()
+    return loss
+
+
 if __name__ == "__main__":
     import argparse
     import json
+    import sys
+    if len(sys.argv) > 1 and sys.argv[1] == "--kernels":    # --kernels [rows]: the kernels alone
+        print(json.dumps({"loss": kernel_passes(int(sys.argv[2]) if len(sys.argv) > 2 else 4096)}))
+        sys.exit(0)
     ap = argparse.ArgumentParser(description="sweep surrogate study (train / held-out / committee queries)")
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--test", type=int, default=200)
