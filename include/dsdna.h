@@ -121,7 +121,9 @@ typedef struct dsdna_params {
   double skin;                           /* neighbour-list skin, at most 1 nm (0: default 0.3) */
   int precision;                         /* DSDNA_PREC_MIXED (FP32 forces, FP64 X/V) or DSDNA_PREC_FP64 */
   int max_neighbors;                     /* neighbour capacity per bead (0: default 32; at most 32) */
-  int block_threads;                     /* threads per CTA of the step kernel (0: default 256; 64..256, multiple of 32) */
+  int block_threads;                     /* threads per CTA of the step kernel, a multiple of 32 in 64..1024
+                                            (FP64 path 64..256); 0: 1024 in mixed precision when the system has
+                                            at least 32 tiles of 32 nucleotides per SM, else 256 */
   int blocks_per_sm;                     /* persistent CTAs per SM (0: as many as fit) */
   int steps_per_graph;                   /* steps per captured CUDA graph launch (0: default 50) */
   /* Sec. 5 denaturation.  A base pair is open when its hydrogen bond is
@@ -142,6 +144,12 @@ typedef struct dsdna_params {
    * launch runs a whole graph chunk of steps), 0 chooses 2 for systems of at
    * most DSDNA_FUSED_REBUILD_MAX_NT nucleotides without a Morton cell table. */
   int rebuild_mode;
+  /* Sec. 2 gives sigma = 1 for steric beads and has ghosts see the other
+   * strand at sigma = 0.5, without saying what two steric beads of opposite
+   * strands use.  The default reading takes sigma_cross for every
+   * cross-strand pair; sigma_cross_steric > 0 gives a pair of steric beads of
+   * opposite strands that sigma instead (the other reading; <= 0: off). */
+  double sigma_cross_steric;
 } dsdna_params;
 
 /* Molecules and (optional) initial state.  NULL X/u builds ideal relaxed
@@ -301,7 +309,7 @@ void dsdna_destroy(dsdna_ctx* ctx);
  * the paper, which ran LAMMPS with hand-set neighbour settings, Sec. 6).
  * Runs trial_steps warm-up steps and trial_steps timed steps of the system
  * sys on temporary contexts for every candidate neighbour skin
- * (0.2 .. 0.6 nm), CTA size (128, 256) and persistent CTAs per SM (and, with
+ * (0.2 .. 0.6 nm), CTA size (128, 256, 1024) and persistent CTAs per SM (and, with
  * rebuild_mode 0 and between a quarter and four times
  * DSDNA_FUSED_REBUILD_MAX_NT nucleotides, both rebuild paths), and writes
  * to *best the copy of *base with the fastest choice (ns per

@@ -28,7 +28,7 @@ class Params(C.Structure):
         "K3", "d_dih", "K4", "lambda_m", "r0_m", "K5", "alpha0", "K6", "mass", "ell", "kT", "gamma", "dt")] + [
         ("seed", C.c_uint64), ("noise", C.c_int), ("steric_phase", C.c_int), ("box", C.c_double * 3),
         ("bubble_rule", C.c_int), ("K2_gc", C.c_double), ("gc", C.c_void_p), ("ring", C.c_void_p),
-        ("removed", C.c_void_p)]
+        ("removed", C.c_void_p), ("sigma_cross_steric", C.c_double)]
 
 
 def build(force: bool = False) -> str:

@@ -64,6 +64,7 @@ void or_default_params(or_params* p) {
   p->kT = 1.0; p->gamma = 1.0; p->dt = 0.005;
   p->seed = 0; p->noise = 1; p->steric_phase = 0;
   p->bubble_rule = 0; p->K2_gc = 0.0; p->gc = NULL; p->ring = NULL; p->removed = NULL;
+  p->sigma_cross_steric = 0.0;
   p->box[0] = p->box[1] = p->box[2] = 0.0;
 }
 
@@ -437,10 +438,15 @@ static void hbond_terms(const or_params* p, const double* X, const double* u, in
 
 /* Typed WCA rule between two beads of the same molecule (Sec. 2, reading
  * A1): two steric beads of one strand use sigma_ss; any two beads of
- * opposite strands use sigma_cross; a ghost never interacts with its own
- * strand.  Returns sigma or 0 for no interaction. */
+ * opposite strands use sigma_cross (with sigma_cross_steric > 0, two steric
+ * beads of opposite strands use that instead: the other reading of A1); a
+ * ghost never interacts with its own strand.  Returns sigma or 0 for no
+ * interaction. */
 static double pair_sigma(const or_params* p, const topo_t* t, int64_t i, int64_t j) {
-  if ((i & 1) != (j & 1)) return p->sigma_cross;
+  if ((i & 1) != (j & 1)) {
+    if (p->sigma_cross_steric > 0.0 && is_steric(p, t, i) && is_steric(p, t, j)) return p->sigma_cross_steric;
+    return p->sigma_cross;
+  }
   if (is_steric(p, t, i) && is_steric(p, t, j)) return p->sigma_ss;
   return 0.0;
 }
@@ -552,7 +558,9 @@ static void all_pairs(const or_params* p, const topo_t* t, const double* X, cons
     }
     return;
   }
-  double rc = pow(2.0, 1.0 / 6.0) * (p->sigma_ss > p->sigma_cross ? p->sigma_ss : p->sigma_cross);
+  double smax = p->sigma_ss > p->sigma_cross ? p->sigma_ss : p->sigma_cross;
+  if (p->sigma_cross_steric > smax) smax = p->sigma_cross_steric;
+  double rc = pow(2.0, 1.0 / 6.0) * smax;
   double h[3]; int64_t nc[3];
   for (int c = 0; c < 3; ++c) {
     if (p->box[c] > 0.0) { nc[c] = (int64_t)floor(p->box[c] / rc); if (nc[c] < 1) nc[c] = 1; h[c] = p->box[c] / (double)nc[c]; }

@@ -78,6 +78,9 @@ typedef struct {
    * every force evaluation, extended by or_run (NULL: nothing removed yet; or_run
    * then keeps its own mask for the run). */
   unsigned char* removed;
+  /* Reading A1 of Sec. 2 taken the other way (opt-in, <= 0: off): sigma of a
+   * pair of steric beads on opposite strands, instead of sigma_cross. */
+  double sigma_cross_steric;
 } or_params;
 
 void or_default_params(or_params* p);

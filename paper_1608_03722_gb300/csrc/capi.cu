@@ -56,7 +56,8 @@ struct dsdna_ctx {
   // kernel instance: with circular molecules or the bubble rule, MODE_EXT;
   // steps with the rebuild inside, MODE_FUSED
   int kernel_flags(int mode) const {
-    return ((n_junc > 0 || p.bubble_rule > 0) ? MODE_EXT : 0) | ((fused && mode == MODE_STEP) ? MODE_FUSED : 0);
+    return ((n_junc > 0 || p.bubble_rule > 0 || p.sigma_cross_steric > 0.0) ? MODE_EXT : 0) |
+           ((fused && mode == MODE_STEP) ? MODE_FUSED : 0);
   }
   int64_t* jslot = nullptr; int* jidx = nullptr; void* jout = nullptr;
   unsigned* cnt = nullptr; unsigned* start = nullptr; int* key = nullptr;
@@ -280,6 +281,8 @@ static void fill_coef(const dsdna_params& p, Coef<Real>& c) {
   c.eps = (Real)p.eps_ev;
   c.sss2 = (Real)(p.sigma_ss * p.sigma_ss); c.rcss2 = (Real)(rc6 * rc6 * p.sigma_ss * p.sigma_ss);
   c.scr2 = (Real)(p.sigma_cross * p.sigma_cross); c.rccr2 = (Real)(rc6 * rc6 * p.sigma_cross * p.sigma_cross);
+  const double scs = p.sigma_cross_steric > 0.0 ? p.sigma_cross_steric : 0.0;
+  c.scs2 = (Real)(scs * scs); c.rccs2 = (Real)(rc6 * rc6 * scs * scs);
   c.K3 = (Real)p.K3; c.cosd = (Real)std::cos(p.d_dih); c.sind = (Real)std::sin(p.d_dih);
   c.K4 = (Real)p.K4; c.lam = (Real)p.lambda_m; c.r0m = (Real)p.r0_m;
   c.K5 = (Real)p.K5; c.alpha0 = (Real)p.alpha0;
@@ -297,7 +300,7 @@ static void fill_coef(const dsdna_params& p, Coef<Real>& c) {
   }
   c.noise_c = (Real)c.noise_cd;
   const double margin = 0.01;   // absorbs FP32 rounding of the wrapped build positions
-  const double rss = rc6 * p.sigma_ss + p.skin + margin, rcr = rc6 * p.sigma_cross + p.skin + margin;
+  const double rss = rc6 * p.sigma_ss + p.skin + margin, rcr = rc6 * std::max(p.sigma_cross, scs) + p.skin + margin;
   c.skin_half2 = (float)(0.25 * p.skin * p.skin);
   c.rl_ss2 = (float)(rss * rss); c.rl_cr2 = (float)(rcr * rcr);
   c.rl_max2 = (float)(std::max(rss, rcr) * std::max(rss, rcr));
@@ -359,8 +362,10 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
   if (p->steric_phase < 0 || p->steric_phase > 2) return fail(nullptr, DSDNA_EINVAL, "steric_phase must be 0, 1 or 2");
   if (p->skin < 0.0 || p->skin > 1.0) return fail(nullptr, DSDNA_EINVAL, "skin must be in [0, 1] nm");
   if (p->max_neighbors < 0 || p->max_neighbors > 32) return fail(nullptr, DSDNA_EINVAL, "max_neighbors must be <= 32");
-  if (p->block_threads && (p->block_threads < 64 || p->block_threads > 256 || p->block_threads % 32))
-    return fail(nullptr, DSDNA_EINVAL, "block_threads must be a multiple of 32 in [64, 256]");
+  if (p->block_threads && (p->block_threads < 64 || p->block_threads > 1024 || p->block_threads % 32))
+    return fail(nullptr, DSDNA_EINVAL, "block_threads must be a multiple of 32 in [64, 1024]");
+  if (p->precision == DSDNA_PREC_FP64 && p->block_threads > 256)
+    return fail(nullptr, DSDNA_EINVAL, "block_threads of the FP64 path must be at most 256");
   if ((s->X == nullptr) != (s->u == nullptr)) return fail(nullptr, DSDNA_EINVAL, "X and u must be given together");
   if (s->circular)
     for (int m = 0; m < s->n_mol; ++m)
@@ -415,13 +420,24 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   c->p = *params;
   if (c->p.skin == 0.0) c->p.skin = 0.3;
   if (c->p.max_neighbors == 0) c->p.max_neighbors = 32;
-  if (c->p.block_threads == 0) c->p.block_threads = 256;
   if (c->p.steps_per_graph <= 0) c->p.steps_per_graph = 50;
-  c->T = c->p.block_threads;
   c->st = (cudaStream_t)cuda_stream;
   if (alloc && alloc->alloc && alloc->release) { c->alloc = *alloc; c->have_alloc = true; }
   auto bad = [&](int code) { g_create_error = c->errmsg; free_all(c); delete c; return code; };
   if (cudaGetDevice(&c->device) != cudaSuccess) return bad(fail(c, DSDNA_ECUDA, "no CUDA device"));
+  if (c->p.block_threads == 0) {
+    // mixed precision with at least one tile per warp at one CTA of 32 warps per
+    // SM: one 1024-thread CTA per SM.  With four 256-thread CTAs per SM the CTAs
+    // launched later finish each step up to 18% later than the first (measured
+    // per warp at 1 Mbp), and the grid barrier waits for the last; otherwise 256.
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    int64_t nt = 0;
+    for (int m = 0; m < sys->n_mol; ++m) nt += 2 * (int64_t)sys->n_bp[m];
+    const bool big = nsm > 0 && (nt + SEG_SLOTS - 1) / SEG_SLOTS >= 32 * (int64_t)nsm;
+    c->p.block_threads = (c->p.precision == DSDNA_PREC_MIXED && big) ? 1024 : 256;
+  }
+  c->T = c->p.block_threads;
   c->n_mol = sys->n_mol;
   c->n_bp.assign(sys->n_bp, sys->n_bp + sys->n_mol);
   c->off.assign(c->n_mol + 1, 0);
@@ -439,7 +455,7 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   // cells per edge (padded to whole 2048-entry scan tiles), Morton index in a
   // smaller periodic box, hash of (molecule, cell) otherwise
   const double rc6 = std::pow(2.0, 1.0 / 6.0);
-  const double rmax = rc6 * std::max(c->p.sigma_ss, c->p.sigma_cross) + c->p.skin + 0.01;
+  const double rmax = rc6 * std::max({c->p.sigma_ss, c->p.sigma_cross, c->p.sigma_cross_steric}) + c->p.skin + 0.01;
   c->cellh = rmax * 1.0001;
   if (c->p.box[0] > 0.0) {
     int bits = 1;
@@ -1113,7 +1129,7 @@ extern "C" int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys,
                               void* cuda_stream, int trial_steps, dsdna_params* best, double* best_ns) {
   if (!base || !sys || !best || trial_steps < 1) return fail(nullptr, DSDNA_EINVAL, "autotune: bad arguments");
   const double skins[] = {0.2, 0.3, 0.4, 0.5, 0.6};
-  const int blocks[] = {128, 256};
+  const int blocks[] = {128, 256, 1024};
   const int per_sm[] = {0, 2};
   cudaStream_t st = (cudaStream_t)cuda_stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1134,6 +1150,7 @@ extern "C" int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys,
   for (double sk : skins)
     for (int T : blocks)
       for (int ps : per_sm) {
+        if (T > 256 && ps > 1) continue;   // one CTA of this size per SM at most
         dsdna_params p = *base;
         p.rebuild_mode = rm;
         p.skin = sk;

@@ -72,6 +72,7 @@ struct Coef {
   Real K1, R02, eps_bb, sbb2, rcbb2;
   Real khb, r0hb, rchb2;
   Real eps, sss2, rcss2, scr2, rccr2;
+  Real scs2, rccs2;  // steric pair across strands under the other reading of Sec. 2 (0: off)
   Real K3, cosd, sind;
   Real K4, lam, r0m;
   Real K5, alpha0;

@@ -334,7 +334,7 @@ __device__ __forceinline__ void store_state(const KArgs<Real>& a, int nxt, int64
 // Forces on nucleotide g from the owner rings, its H-bond and its list
 // pairs, then (MODE_STEP) its Langevin update; MODE_FORCES writes the site
 // forces, MODE_ENERGY adds its per-nucleotide energies.
-template <class Real, int MODE>
+template <class Real, int MODE, bool EXT>
 __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t g, int cur,
                                                 int64_t step, unsigned& fl) {
   const int nxt = cur ^ 1;
@@ -424,8 +424,15 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
         }
         const V3<Real> d = R - h * uj + h * um;   // bead_j - bead_me
         const bool cross_strand = ((g ^ j) & 1) != 0;
+        Real s2 = cross_strand ? a.c.scr2 : a.c.sss2, rc2 = cross_strand ? a.c.rccr2 : a.c.rcss2;
+        if constexpr (EXT) {   // the other reading of Sec. 2: two steric beads across strands
+          if (cross_strand && a.c.scs2 > (Real)0 && (f & F_STERIC) && (a.topo[(unsigned)j] & F_STERIC)) {
+            s2 = a.c.scs2;
+            rc2 = a.c.rccs2;
+          }
+        }
         Real e;
-        const V3<Real> fw = t_wca(a.c, d, cross_strand ? a.c.scr2 : a.c.sss2, cross_strand ? a.c.rccr2 : a.c.rcss2, &e);
+        const V3<Real> fw = t_wca(a.c, d, s2, rc2, &e);
         Fb += fw;
         if constexpr (MODE == MODE_ENERGY) {
           Eb[3] += (Real)0.5 * e;
@@ -578,7 +585,7 @@ __device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_
     }
     owner_pass<Real, MODE, EXT>(a, sm, B + 2 + lane, cur, B + 2 + lane < s1, fl);
     __syncwarp();
-    if (B + lane < s1) nucleotide_pass<Real, MODE>(a, sm, B + lane, cur, step, fl);
+    if (B + lane < s1) nucleotide_pass<Real, MODE, EXT>(a, sm, B + lane, cur, step, fl);
   }
   __syncwarp();
 }
@@ -620,13 +627,19 @@ __device__ unsigned fused_rebuild(const KArgs<Real>& a, const SegSmem<Real>& sm,
 // null: nsteps), one bounded grid barrier per step; stop early when a bead
 // moved more than skin/2 (the rebuild kernels run next) or on an error.
 // MODE_FORCES / MODE_ENERGY: one pass with the current list.
-// EXT: the instance for systems with circular molecules or the bubble rule
-// (junction pass, open-pair marks, removed terms); the other instance
-// compiles none of it.  FUSED (MODE_STEP): a stale list is rebuilt inside the
-// kernel (fused_rebuild) and the steps go on, instead of returning so that
-// the rebuild kernels run.
+// EXT: the instance for systems with circular molecules, the bubble rule or
+// steric pairs across strands (junction pass, open-pair marks, removed
+// terms, the partner's steric flag); the other instance compiles none of it.
+// FUSED (MODE_STEP): a stale list is rebuilt inside the kernel
+// (fused_rebuild) and the steps go on, instead of returning so that the
+// rebuild kernels run.
+// Mixed precision runs CTAs of up to 1024 threads at 64 registers (one CTA
+// of 32 warps per SM, or four of 8); FP64 CTAs of up to 256 threads.
+template <class Real>
+__host__ __device__ constexpr int engine_max_threads() { return sizeof(Real) == 4 ? 1024 : 256; }
+
 template <class Real, int MODE, int CAPMAX, bool EXT, bool FUSED = false>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 1) engine_kernel(const __grid_constant__ KArgs<Real> a) {
+__global__ void __launch_bounds__(engine_max_threads<Real>(), 1) engine_kernel(const __grid_constant__ KArgs<Real> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned s_word;
   __shared__ unsigned s_fl;

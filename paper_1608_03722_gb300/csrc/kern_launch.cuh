@@ -27,13 +27,19 @@ static const void* engine_fn(int mode) {
   return (mode & MODE_EXT) ? engine_fn_ext<Real, true>(mode) : engine_fn_ext<Real, false>(mode);
 }
 
-// Largest co-resident grid for the cooperative launch of `mode` with T threads.
+// Largest co-resident grid for the cooperative launch of `mode` with T threads
+// (T above engine_max_threads<Real>() has no resident CTA: 0).
 template <class Real>
 cudaError_t engine_occupancy(int mode, int T, int* blocks_per_sm, size_t* smem) {
+  if (T > engine_max_threads<Real>()) {
+    *blocks_per_sm = 0;
+    return cudaSuccess;
+  }
   *smem = seg_smem_bytes<Real>(T);
   const void* fn = engine_fn<Real>(mode);
   // the attribute is per kernel, shared by every context: allow the largest CTA any context may use
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg_smem_bytes<Real>(256));
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)seg_smem_bytes<Real>(engine_max_threads<Real>()));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, T, *smem);
 }

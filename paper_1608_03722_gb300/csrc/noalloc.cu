@@ -174,7 +174,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   if (q.skin == 0.0) q.skin = 0.3;
   const double skin = q.skin;
   const double rc6 = std::pow(2.0, 1.0 / 6.0);
-  const double cellh = (rc6 * std::max(p->sigma_ss, p->sigma_cross) + skin + 0.01) * 1.0001;
+  const double cellh = (rc6 * std::max({p->sigma_ss, p->sigma_cross, p->sigma_cross_steric}) + skin + 0.01) * 1.0001;
   const bool periodic = p->box[0] > 0.0;
   int nc[3] = {0, 0, 0};
   unsigned H = 1024;
@@ -214,6 +214,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   a.n = n; a.ns = NA_MAX_NT; a.n_mol = n_mol; a.nseg = (n + 31) / 32; a.cap = NA_CAP;
   a.nsteps = 0; a.noise_mode = 0; a.seed_lo = 0; a.seed_hi = 0;
   a.bubble = p->bubble_rule ? 1 : 0;   // one evaluation without history: rule 2 removes what rule 1 does
+  const bool ext = a.bubble || p->sigma_cross_steric > 0.0;
   a.n_junc = 0; a.jslot = nullptr; a.jidx = nullptr; a.jout = nullptr;   // linear molecules only
   a.spin_budget = 4000000000ull;
   a.X = reinterpret_cast<double*>(b + O_X);
@@ -268,8 +269,9 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(s->grid, (n + NA_T - 1) / NA_T));
   const int scan_grid = (int)std::min<int64_t>(NA_MAX_GRID, std::max<int64_t>(1, ((int64_t)H + 2047) / 2048));
   e = rebuild_launch<float>(a, scan_grid, st);
-  // the bubble rule runs in the kernel instance that has it (same launch bounds, so the same grid fits)
-  if (e == cudaSuccess) e = engine_launch<float>(MODE_FORCES | (a.bubble ? MODE_EXT : 0), a, grid, NA_T, s->smem, st);
+  // the bubble rule and the steric pair across strands run in the kernel instance that has them
+  // (same launch bounds, so the same grid fits)
+  if (e == cudaSuccess) e = engine_launch<float>(MODE_FORCES | (ext ? MODE_EXT : 0), a, grid, NA_T, s->smem, st);
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
   k_noalloc_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.fout, n, F_bead, F_patch);
   e = cudaGetLastError();

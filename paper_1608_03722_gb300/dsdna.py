@@ -33,7 +33,7 @@ class dsdna_params(C.Structure):
         ("seed", C.c_uint64), ("noise", C.c_int), ("steric_phase", C.c_int), ("box", C.c_double * 3),
         ("skin", C.c_double), ("precision", C.c_int), ("max_neighbors", C.c_int), ("block_threads", C.c_int),
         ("blocks_per_sm", C.c_int), ("steps_per_graph", C.c_int), ("bubble_rule", C.c_int), ("K2_gc", C.c_double),
-        ("rebuild_mode", C.c_int)]
+        ("rebuild_mode", C.c_int), ("sigma_cross_steric", C.c_double)]
 
 
 class dsdna_system(C.Structure):
