@@ -11,7 +11,8 @@
  *     between consecutive beads of a strand, breakable harmonic hydrogen bond
  *     between paired patches, typed WCA excluded volume between beads (steric
  *     beads every third nucleotide, ghosts interacting only with the other
- *     strand at sigma = 0.5, Sec. 2 / Fig. 1d), dihedral A-E-F-B, Morse
+ *     strand at sigma = 0.5 and steric beads see each other at sigma = 1
+ *     on either strand, Sec. 2 / Fig. 1d), dihedral A-E-F-B, Morse
  *     stacking between consecutive patches, planarity angle E-F-B and
  *     Kratky-Porod bending of three consecutive patches.
  *   - Langevin dynamics (App. A Eq. 8) with the velocity-Verlet step of
@@ -106,7 +107,7 @@ enum { DSDNA_NOISE_OFF = 0, DSDNA_NOISE_UNIFORM = 1, DSDNA_NOISE_GAUSSIAN = 2 };
 typedef struct dsdna_params {
   double K1, R0, eps_bb, sigma_bb;       /* FENE + backbone WCA */
   double K2, r0_hb, rc_hb;               /* hydrogen bond */
-  double eps_ev, sigma_ss, sigma_cross;  /* steric WCA: steric pair of one strand / any pair across strands */
+  double eps_ev, sigma_ss, sigma_cross;  /* steric WCA: two steric beads / a pair across strands with a ghost */
   double K3, d_dih;                      /* dihedral, d in radians (-144 deg) */
   double K4, lambda_m, r0_m;             /* Morse stacking */
   double K5, alpha0;                     /* planarity (K5/2)(alpha - alpha0)^2, alpha0 in radians */
@@ -146,9 +147,9 @@ typedef struct dsdna_params {
   int rebuild_mode;
   /* Sec. 2 gives sigma = 1 for steric beads and has ghosts see the other
    * strand at sigma = 0.5, without saying what two steric beads of opposite
-   * strands use.  The default reading takes sigma_cross for every
-   * cross-strand pair; sigma_cross_steric > 0 gives a pair of steric beads of
-   * opposite strands that sigma instead (the other reading; <= 0: off). */
+   * strands use.  sigma_cross_steric is that sigma: 1 by default (the steric
+   * size, the reading whose torsional persistence length matches Sec. 3.2);
+   * <= 0 gives such pairs sigma_cross like every other cross-strand pair. */
   double sigma_cross_steric;
 } dsdna_params;
 

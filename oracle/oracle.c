@@ -64,7 +64,7 @@ void or_default_params(or_params* p) {
   p->kT = 1.0; p->gamma = 1.0; p->dt = 0.005;
   p->seed = 0; p->noise = 1; p->steric_phase = 0;
   p->bubble_rule = 0; p->K2_gc = 0.0; p->gc = NULL; p->ring = NULL; p->removed = NULL;
-  p->sigma_cross_steric = 0.0;
+  p->sigma_cross_steric = 1.0;   /* reading A1: two steric beads at sigma = 1 on either strand */
   p->box[0] = p->box[1] = p->box[2] = 0.0;
 }
 
@@ -437,11 +437,11 @@ static void hbond_terms(const or_params* p, const double* X, const double* u, in
 }
 
 /* Typed WCA rule between two beads of the same molecule (Sec. 2, reading
- * A1): two steric beads of one strand use sigma_ss; any two beads of
- * opposite strands use sigma_cross (with sigma_cross_steric > 0, two steric
- * beads of opposite strands use that instead: the other reading of A1); a
- * ghost never interacts with its own strand.  Returns sigma or 0 for no
- * interaction. */
+ * A1): two steric beads of one strand use sigma_ss, two steric beads of
+ * opposite strands sigma_cross_steric (1 by default, the steric size; <= 0:
+ * sigma_cross, the other reading), any other pair of opposite strands
+ * sigma_cross (ghosts see the other strand at 0.5); a ghost never interacts
+ * with its own strand.  Returns sigma or 0 for no interaction. */
 static double pair_sigma(const or_params* p, const topo_t* t, int64_t i, int64_t j) {
   if ((i & 1) != (j & 1)) {
     if (p->sigma_cross_steric > 0.0 && is_steric(p, t, i) && is_steric(p, t, j)) return p->sigma_cross_steric;

@@ -51,7 +51,7 @@ typedef struct {
   /* Table 1 */
   double K1, R0, eps_bb, sigma_bb;     /* FENE + backbone WCA */
   double K2, r0_hb, rc_hb;             /* hydrogen bond */
-  double eps_ev, sigma_ss, sigma_cross;/* steric WCA: same strand / cross strand */
+  double eps_ev, sigma_ss, sigma_cross;/* steric WCA: two steric beads / cross-strand pair with a ghost */
   double K3, d_dih;                    /* dihedral, d in radians */
   double K4, lambda_m, r0_m;           /* Morse stacking */
   double K5, alpha0;                   /* planarity, alpha0 in radians */
@@ -78,8 +78,9 @@ typedef struct {
    * every force evaluation, extended by or_run (NULL: nothing removed yet; or_run
    * then keeps its own mask for the run). */
   unsigned char* removed;
-  /* Reading A1 of Sec. 2 taken the other way (opt-in, <= 0: off): sigma of a
-   * pair of steric beads on opposite strands, instead of sigma_cross. */
+  /* Sec. 2, reading A1: sigma of a pair of steric beads on opposite strands
+   * (default 1, the steric size); <= 0 gives such pairs sigma_cross like any
+   * other cross-strand pair (the other reading). */
   double sigma_cross_steric;
 } or_params;
 

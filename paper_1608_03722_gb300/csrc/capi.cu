@@ -56,8 +56,7 @@ struct dsdna_ctx {
   // kernel instance: with circular molecules or the bubble rule, MODE_EXT;
   // steps with the rebuild inside, MODE_FUSED
   int kernel_flags(int mode) const {
-    return ((n_junc > 0 || p.bubble_rule > 0 || p.sigma_cross_steric > 0.0) ? MODE_EXT : 0) |
-           ((fused && mode == MODE_STEP) ? MODE_FUSED : 0);
+    return ((n_junc > 0 || p.bubble_rule > 0) ? MODE_EXT : 0) | ((fused && mode == MODE_STEP) ? MODE_FUSED : 0);
   }
   int64_t* jslot = nullptr; int* jidx = nullptr; void* jout = nullptr;
   unsigned* cnt = nullptr; unsigned* start = nullptr; int* key = nullptr;
@@ -300,10 +299,12 @@ static void fill_coef(const dsdna_params& p, Coef<Real>& c) {
   }
   c.noise_c = (Real)c.noise_cd;
   const double margin = 0.01;   // absorbs FP32 rounding of the wrapped build positions
-  const double rss = rc6 * p.sigma_ss + p.skin + margin, rcr = rc6 * std::max(p.sigma_cross, scs) + p.skin + margin;
+  const double rss = rc6 * p.sigma_ss + p.skin + margin, rcr = rc6 * p.sigma_cross + p.skin + margin;
   c.skin_half2 = (float)(0.25 * p.skin * p.skin);
-  c.rl_ss2 = (float)(rss * rss); c.rl_cr2 = (float)(rcr * rcr);
-  c.rl_max2 = (float)(std::max(rss, rcr) * std::max(rss, rcr));
+  const double rcs = scs > 0.0 ? rc6 * scs + p.skin + margin : rcr;   // steric pairs across strands
+  c.rl_ss2 = (float)(rss * rss); c.rl_cr2 = (float)(rcr * rcr); c.rl_cs2 = (float)(rcs * rcs);
+  const double rmx = std::max({rss, rcr, rcs});
+  c.rl_max2 = (float)(rmx * rmx);
 }
 
 namespace dsdna {
@@ -408,6 +409,7 @@ extern "C" void dsdna_default_params(dsdna_params* p) {
   p->kT = 1.0; p->gamma = 1.0; p->dt = 0.005;                             // App. A, Eq. 16
   p->seed = 0; p->noise = DSDNA_NOISE_UNIFORM; p->steric_phase = 0;
   p->skin = 0.3; p->precision = DSDNA_PREC_MIXED;
+  p->sigma_cross_steric = 1.0;   // Sec. 2, reading A1: two steric beads at sigma = 1 on either strand
 }
 
 extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys, const dsdna_allocator* alloc,

@@ -85,7 +85,7 @@ struct Coef {
   Real halfdtM, halfdtI;
   Real M, I;
   float skin_half2;  // (skin/2)^2
-  float rl_ss2, rl_cr2, rl_max2;
+  float rl_ss2, rl_cr2, rl_cs2, rl_max2;
   Real khb_gc;       // hydrogen-bond coefficient of G.C pairs (Sec. 5)
   double dt_d;       // FP64 step for the position accumulation
   double noise_cd;   // FP64 copy of noise_c
@@ -319,8 +319,9 @@ __device__ __forceinline__ void load_slot(const KArgs<Real>& a, int cur, int64_t
 }
 
 __device__ __forceinline__ int img_comp(int packed, int c) {
-  return ((int)((unsigned)packed << (22 - 10 * c))) >> 22;   // signed 10-bit field c
+  return ((int)((unsigned)packed << (22 - 10 * c))) >> 22;   // signed 10-bit field c (bits 30, 31 ignored)
 }
+constexpr int IMG_STERIC_SHIFT = 30;   // steric flag of the bead in its image word
 
 // ---------------------------------------------------------------- interaction terms
 // Each returns the force on the second site (first gets the opposite) or the

@@ -23,6 +23,8 @@ struct SegSmem {
   Real* cs;          // [6][RING] forces of owner terms on the owner (bead xyz, patch xyz)
   Real* cn;          // [6][RING] ... on the owner's next nucleotide
   Real* cp;          // [3][RING] ... on the owner's previous patch (bending)
+  int* pst;          // [SEG] first pair index of each nucleotide of the tile (warp_pairs)
+  Real* pf;          // [2 SEG][3] pair forces of one round of warp_pairs
 };
 
 template <class Real>
@@ -30,6 +32,7 @@ __host__ __device__ constexpr size_t seg_warp_bytes() {
   size_t b = sizeof(SPos<Real>) * RING + sizeof(int) * RING;
   b = (b + 15) & ~(size_t)15;
   b += sizeof(Real) * (size_t)RING * 15;
+  b += sizeof(int) * 32 + sizeof(Real) * 2 * 32 * 3;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -49,6 +52,8 @@ __device__ __forceinline__ SegSmem<Real> carve(unsigned char* raw, int /*T*/) {
   s.cs = reinterpret_cast<Real*>(w + off);
   s.cn = s.cs + (size_t)RING * 6;
   s.cp = s.cn + (size_t)RING * 6;
+  s.pf = s.cp + (size_t)RING * 3;
+  s.pst = reinterpret_cast<int*>(s.pf + 2 * 32 * 3);
   return s;
 }
 
@@ -331,12 +336,137 @@ __device__ __forceinline__ void store_state(const KArgs<Real>& a, int nxt, int64
   }
 }
 
+// Own periodic image word of slot gu (image fields and steric flag): in mixed
+// precision the fourth word of the mirror (staged a tile ago and still
+// cached); the FP64 path keeps it apart.
+template <class Real>
+__device__ __forceinline__ int own_image(const KArgs<Real>& a, int cur, unsigned gu) {
+  if constexpr (sizeof(Real) == 4) return a.Kw[(unsigned)cur * (unsigned)a.ns + gu].w;
+  else return a.img[gu];
+}
+
+// Typed WCA force (App. A Eq. 11) on the bead of slot gu (staged record me,
+// orientation um, flags f, image word img_me) from its list entry ent; the
+// bead separation and the pair energy go to *dout, *eout when given.
+template <class Real>
+__device__ __forceinline__ V3<Real> pair_force(const KArgs<Real>& a, int cur, unsigned gu, const SPos<Real>& me,
+                                               V3<Real> um, int f, int img_me, int ent, V3<Real>* dout, Real* eout) {
+  const unsigned ns = (unsigned)a.ns;
+  const Real h = a.c.h;
+  const int j = ent & ENT_JMASK;
+  V3<Real> R;
+  V3<Real> uj;
+  int wj;   // the partner's image word (periodic image, steric flag)
+  if constexpr (sizeof(Real) == 4) {
+    const int4 kj = a.Kw[(unsigned)cur * ns + (unsigned)j];
+    const float4 u4 = a.U[(unsigned)cur * ns + (unsigned)j];
+    wj = kj.w;
+    uj = V3<float>{u4.x, u4.y, u4.z};
+    unsigned dx = (unsigned)kj.x - (unsigned)me.kx, dy = (unsigned)kj.y - (unsigned)me.ky,
+             dz = (unsigned)kj.z - (unsigned)me.kz;
+    if (a.periodic) {
+      const int mx = img_comp(img_me, 0) - img_comp(kj.w, 0) + ent_shift(ent, 0);
+      const int my = img_comp(img_me, 1) - img_comp(kj.w, 1) + ent_shift(ent, 1);
+      const int mz = img_comp(img_me, 2) - img_comp(kj.w, 2) + ent_shift(ent, 2);
+      dx += (unsigned)mx * a.Lfix[0]; dy += (unsigned)my * a.Lfix[1]; dz += (unsigned)mz * a.Lfix[2];
+    }
+    R = V3<float>{(float)(int)dx * FIX_SCALE_F, (float)(int)dy * FIX_SCALE_F, (float)(int)dz * FIX_SCALE_F};
+  } else {
+    const double* X = a.X + (size_t)cur * 3 * a.ns;
+    const double* ud = a.ud + (size_t)cur * 3 * a.ns;
+    uj = V3<double>{ud[(unsigned)j], ud[ns + (unsigned)j], ud[2 * ns + (unsigned)j]};
+    R = V3<double>{X[(unsigned)j] - me.x, X[ns + (unsigned)j] - me.y, X[2 * ns + (unsigned)j] - me.z};
+    wj = a.img[j];
+    if (a.periodic) {
+      R.x += (double)(img_comp(img_me, 0) - img_comp(wj, 0) + ent_shift(ent, 0)) * a.L[0];
+      R.y += (double)(img_comp(img_me, 1) - img_comp(wj, 1) + ent_shift(ent, 1)) * a.L[1];
+      R.z += (double)(img_comp(img_me, 2) - img_comp(wj, 2) + ent_shift(ent, 2)) * a.L[2];
+    }
+  }
+  const V3<Real> d = R - h * uj + h * um;   // bead_j - bead_me
+  const bool cross_strand = ((gu ^ (unsigned)j) & 1u) != 0;
+  // typed sigma (Sec. 2, reading A1): two steric beads (either strand) at
+  // sigma_ss, or at sigma_cross_steric across strands when that is set; any
+  // other pair across strands at sigma_cross.  The partner's steric flag is
+  // bit 30 of its image word.
+  const bool st2 = (f & F_STERIC) && ((wj >> IMG_STERIC_SHIFT) & 1);
+  Real s2 = a.c.sss2, rc2 = a.c.rcss2;
+  if (cross_strand) {
+    const bool cs = st2 && a.c.scs2 > (Real)0;
+    s2 = cs ? a.c.scs2 : a.c.scr2;
+    rc2 = cs ? a.c.rccs2 : a.c.rccr2;
+  }
+  Real e;
+  const V3<Real> fw = t_wca(a.c, d, s2, rc2, &e);
+  if (dout) *dout = d;
+  if (eout) *eout = e;
+  return fw;
+}
+
+// The list pairs of the tile's nucleotides B .. B+31 spread evenly over the
+// warp's lanes (warp-collective; `act` false for a lane past the strip): the
+// pairs are numbered nucleotide by nucleotide (an exclusive scan of the list
+// counts), each lane evaluates pairs lane, lane + 32, ... in rounds of 64
+// into the shared buffer, and each nucleotide's lane then adds its own pair
+// forces to Fb in list order.  The warp iterates as often as the tile has
+// pairs / 32, not as often as its fullest list; steric beads hold most
+// pairs (about five against none for a ghost in the relaxed helix).
+template <class Real>
+__device__ __forceinline__ void warp_pairs(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t g, bool act, int cur,
+                                           V3<Real>& Fb) {
+  const int lane = threadIdx.x & 31;
+  const int64_t B = g - lane;
+  const unsigned ns = (unsigned)a.ns;
+  const int nn = act ? a.ncnt[(unsigned)g] : 0;
+  int incl = nn;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;
+  const int excl = incl - nn;
+  sm.pst[lane] = excl;
+  __syncwarp();
+  for (int c0 = 0; c0 < total; c0 += 2 * SEG) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int p = c0 + k * SEG + lane;
+      if (p < total) {
+        int L = 0;   // the nucleotide (lane) the pair belongs to: last first-index <= p
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1)
+          if (sm.pst[L + st] <= p) L += st;
+        const unsigned gL = (unsigned)(B + L);
+        const int rL = ring(B + L);
+        const int fL = sm.flg[rL];
+        const SPos<Real>& mL = sm.pos[rL];
+        const int img = a.periodic ? own_image(a, cur, gL) : 0;
+        const int ent = a.nbr[(unsigned)(p - sm.pst[L]) * ns + gL];
+        const V3<Real> fw = pair_force(a, cur, gL, mL, uvec(mL), fL, img, ent, (V3<Real>*)nullptr, (Real*)nullptr);
+        Real* o = sm.pf + 3 * (k * SEG + lane);
+        o[0] = fw.x; o[1] = fw.y; o[2] = fw.z;
+      }
+    }
+    __syncwarp();
+    if (nn) {
+      const int p0 = excl > c0 ? excl : c0, p1 = excl + nn < c0 + 2 * SEG ? excl + nn : c0 + 2 * SEG;
+      for (int p = p0; p < p1; ++p) {
+        const Real* o = sm.pf + 3 * (p - c0);
+        Fb += V3<Real>{o[0], o[1], o[2]};
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Forces on nucleotide g from the owner rings, its H-bond and its list
 // pairs, then (MODE_STEP) its Langevin update; MODE_FORCES writes the site
 // forces, MODE_ENERGY adds its per-nucleotide energies.
 template <class Real, int MODE, bool EXT>
-__device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t g, int cur,
-                                                int64_t step, unsigned& fl) {
+__device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_t g, bool act,
+                                                int cur, int64_t step, unsigned& fl) {
   const int nxt = cur ^ 1;
   const unsigned ns = (unsigned)a.ns, gu = (unsigned)g;   // slot indices stay below 2^26: 32-bit index arithmetic
   Real Eb[NTERMS];
@@ -347,12 +477,14 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
   }
   {
     const int ri = ring(g);
-    const int f = sm.flg[ri];
+    const int f = act ? sm.flg[ri] : 0;
     const SPos<Real>& me = sm.pos[ri];
     const Real h = a.c.h;
     const V3<Real> um = uvec(me);
-    V3<Real> Fb{sm.cs[0 * RING + ri], sm.cs[1 * RING + ri], sm.cs[2 * RING + ri]};
-    V3<Real> Fp{sm.cs[3 * RING + ri], sm.cs[4 * RING + ri], sm.cs[5 * RING + ri]};
+    V3<Real> Fb{0, 0, 0}, Fp{0, 0, 0};
+    if (act) {
+    Fb = V3<Real>{sm.cs[0 * RING + ri], sm.cs[1 * RING + ri], sm.cs[2 * RING + ri]};
+    Fp = V3<Real>{sm.cs[3 * RING + ri], sm.cs[4 * RING + ri], sm.cs[5 * RING + ri]};
     const int dir = (g & 1) ? -2 : 2;
     // (a neighbour across a ring's junction has its flag cleared here: its
     // owner's forces arrive through cs, see owner_terms)
@@ -385,61 +517,26 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
         }
       }
     }
-    // typed WCA pairs (App. A Eq. 11) from the neighbour list
-    {
-      const int nn = a.ncnt[gu];
-      // own periodic image: in mixed precision the image word of the mirror
-      // (Kw.w, staged a tile ago and still cached); the FP64 path keeps it apart
-      int img_me = 0;
-      if (a.periodic) img_me = sizeof(Real) == 4 ? a.Kw[(unsigned)cur * ns + gu].w : a.img[gu];
-      for (int q = 0; q < nn; ++q) {
-        const int ent = a.nbr[(unsigned)q * ns + gu];
-        const int j = ent & ENT_JMASK;
-        V3<Real> R;
-        V3<Real> uj;
-        if constexpr (sizeof(Real) == 4) {
-          const int4 kj = a.Kw[(unsigned)cur * ns + (unsigned)j];
-          const float4 u4 = a.U[(unsigned)cur * ns + (unsigned)j];
-          uj = V3<float>{u4.x, u4.y, u4.z};
-          unsigned dx = (unsigned)kj.x - (unsigned)me.kx, dy = (unsigned)kj.y - (unsigned)me.ky,
-                   dz = (unsigned)kj.z - (unsigned)me.kz;
-          if (a.periodic) {
-            const int mx = img_comp(img_me, 0) - img_comp(kj.w, 0) + ent_shift(ent, 0);
-            const int my = img_comp(img_me, 1) - img_comp(kj.w, 1) + ent_shift(ent, 1);
-            const int mz = img_comp(img_me, 2) - img_comp(kj.w, 2) + ent_shift(ent, 2);
-            dx += (unsigned)mx * a.Lfix[0]; dy += (unsigned)my * a.Lfix[1]; dz += (unsigned)mz * a.Lfix[2];
-          }
-          R = V3<float>{(float)(int)dx * FIX_SCALE_F, (float)(int)dy * FIX_SCALE_F, (float)(int)dz * FIX_SCALE_F};
-        } else {
-          const double* X = a.X + (size_t)cur * 3 * a.ns;
-          const double* ud = a.ud + (size_t)cur * 3 * a.ns;
-          uj = V3<double>{ud[(unsigned)j], ud[ns + (unsigned)j], ud[2 * ns + (unsigned)j]};
-          R = V3<double>{X[(unsigned)j] - me.x, X[ns + (unsigned)j] - me.y, X[2 * ns + (unsigned)j] - me.z};
-          if (a.periodic) {
-            const int ij = a.img[j];
-            R.x += (double)(img_comp(img_me, 0) - img_comp(ij, 0) + ent_shift(ent, 0)) * a.L[0];
-            R.y += (double)(img_comp(img_me, 1) - img_comp(ij, 1) + ent_shift(ent, 1)) * a.L[1];
-            R.z += (double)(img_comp(img_me, 2) - img_comp(ij, 2) + ent_shift(ent, 2)) * a.L[2];
-          }
-        }
-        const V3<Real> d = R - h * uj + h * um;   // bead_j - bead_me
-        const bool cross_strand = ((g ^ j) & 1) != 0;
-        Real s2 = cross_strand ? a.c.scr2 : a.c.sss2, rc2 = cross_strand ? a.c.rccr2 : a.c.rcss2;
-        if constexpr (EXT) {   // the other reading of Sec. 2: two steric beads across strands
-          if (cross_strand && a.c.scs2 > (Real)0 && (f & F_STERIC) && (a.topo[(unsigned)j] & F_STERIC)) {
-            s2 = a.c.scs2;
-            rc2 = a.c.rccs2;
-          }
-        }
-        Real e;
-        const V3<Real> fw = t_wca(a.c, d, s2, rc2, &e);
-        Fb += fw;
-        if constexpr (MODE == MODE_ENERGY) {
+    }
+    // typed WCA pairs (App. A Eq. 11) from the neighbour list: spread over the
+    // warp's lanes (warp_pairs), or one lane per nucleotide with energies
+    if constexpr (MODE == MODE_ENERGY) {
+      if (act) {
+        const int nn = a.ncnt[gu];
+        const int img_me = a.periodic ? own_image(a, cur, gu) : 0;
+        for (int q = 0; q < nn; ++q) {
+          V3<Real> d;
+          Real e;
+          const V3<Real> fw = pair_force(a, cur, gu, me, um, f, img_me, a.nbr[(unsigned)q * ns + gu], &d, &e);
+          Fb += fw;
           Eb[3] += (Real)0.5 * e;
           vir_add(Wb, d, (Real)-0.5 * fw);
         }
       }
+    } else {
+      warp_pairs(a, sm, g, act, cur, Fb);
     }
+    if (!act) return;
     // applied load on the last base pair (Sec. 4.1, 4.2): f/2 at each centre,
     // torque as a couple normal to its axis; half on each site
     if (f & F_TOP) {
@@ -480,7 +577,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       int kr[3] = {0, 0, 0}, packed = 0;
       if constexpr (MODE == MODE_STEP) {
         kr[0] = a.kref[gu]; kr[1] = a.kref[ns + gu]; kr[2] = a.kref[2 * ns + gu];
-        if constexpr (sizeof(Real) == 4) packed = a.periodic ? a.Kw[(unsigned)cur * ns + gu].w : 0;
+        if constexpr (sizeof(Real) == 4) packed = a.Kw[(unsigned)cur * ns + gu].w;   // image and steric flag carried
       }
       const bool frozen = (f & F_FROZEN) != 0;
       V3<Real> Ft{0, 0, 0}, Tt{0, 0, 0};
@@ -550,7 +647,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       }
     }
   }
-  if constexpr (MODE == MODE_ENERGY) flush_energy(a, sm.flg[ring(g)] >> MOL_SHIFT, Eb, Wb);
+  if constexpr (MODE == MODE_ENERGY) flush_energy(a, sm.flg[ring(g)] >> MOL_SHIFT, Eb, Wb);   // act here
 }
 
 // One warp's strip: tiles [t0, t1) of SEG slots.  The prologue stages slots
@@ -585,7 +682,7 @@ __device__ void strip_pass(const KArgs<Real>& a, const SegSmem<Real>& sm, int64_
     }
     owner_pass<Real, MODE, EXT>(a, sm, B + 2 + lane, cur, B + 2 + lane < s1, fl);
     __syncwarp();
-    if (B + lane < s1) nucleotide_pass<Real, MODE, EXT>(a, sm, B + lane, cur, step, fl);
+    nucleotide_pass<Real, MODE, EXT>(a, sm, B + lane, B + lane < s1, cur, step, fl);   // warp-collective
   }
   __syncwarp();
 }

@@ -214,7 +214,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   a.n = n; a.ns = NA_MAX_NT; a.n_mol = n_mol; a.nseg = (n + 31) / 32; a.cap = NA_CAP;
   a.nsteps = 0; a.noise_mode = 0; a.seed_lo = 0; a.seed_hi = 0;
   a.bubble = p->bubble_rule ? 1 : 0;   // one evaluation without history: rule 2 removes what rule 1 does
-  const bool ext = a.bubble || p->sigma_cross_steric > 0.0;
+  const bool ext = a.bubble != 0;
   a.n_junc = 0; a.jslot = nullptr; a.jidx = nullptr; a.jout = nullptr;   // linear molecules only
   a.spin_budget = 4000000000ull;
   a.X = reinterpret_cast<double*>(b + O_X);
@@ -269,8 +269,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(s->grid, (n + NA_T - 1) / NA_T));
   const int scan_grid = (int)std::min<int64_t>(NA_MAX_GRID, std::max<int64_t>(1, ((int64_t)H + 2047) / 2048));
   e = rebuild_launch<float>(a, scan_grid, st);
-  // the bubble rule and the steric pair across strands run in the kernel instance that has them
-  // (same launch bounds, so the same grid fits)
+  // the bubble rule runs in the kernel instance that has it (same launch bounds, so the same grid fits)
   if (e == cudaSuccess) e = engine_launch<float>(MODE_FORCES | (ext ? MODE_EXT : 0), a, grid, NA_T, s->smem, st);
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
   k_noalloc_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.fout, n, F_bead, F_patch);

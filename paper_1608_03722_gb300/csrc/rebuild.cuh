@@ -39,6 +39,15 @@ __device__ __forceinline__ unsigned hash_block(int mol, int bx, int cy, int cz) 
 // are then one range each.
 constexpr int HASH_X_OFF = 4;
 
+// Squared list radius of a bead pair by type (Sec. 2, reading A1): two steric
+// beads (either strand) at the steric radius, any other pair across strands
+// at the cross-strand radius, a ghost and a bead of its own strand not at all
+// (negative).  With the cross-strand steric reading off, rl_cs2 = rl_cr2.
+template <class Real>
+__device__ __forceinline__ float list_r2(const Coef<Real>& c, bool cross, bool both_steric) {
+  return cross ? (both_steric ? c.rl_cs2 : c.rl_cr2) : (both_steric ? c.rl_ss2 : -1.0f);
+}
+
 template <class Real>
 __device__ __forceinline__ unsigned cell_key(const KArgs<Real>& a, int mol, int cx, int cy, int cz) {
   if (a.table == TABLE_LINEAR) return (unsigned)cx + (unsigned)a.nc[0] * ((unsigned)cy + (unsigned)a.nc[1] * (unsigned)cz);
@@ -111,8 +120,11 @@ __device__ void rebuild_bin(const KArgs<Real>& a, int cur, unsigned& fl) {
         ci[c] = (int)floorf(x * a.invcellh[c]);
       }
     }
-    const int packed = (w[0] & 0x3ff) | ((w[1] & 0x3ff) << 10) | ((w[2] & 0x3ff) << 20);
-    const int mol = a.topo[g] >> MOL_SHIFT;
+    // the image word (three signed 10-bit fields) also carries the bead's steric
+    // flag in bit 30, for the pair typing of the force loop
+    const int tp = a.topo[g];
+    const int packed = (w[0] & 0x3ff) | ((w[1] & 0x3ff) << 10) | ((w[2] & 0x3ff) << 20) | ((tp & F_STERIC) << IMG_STERIC_SHIFT);
+    const int mol = tp >> MOL_SHIFT;
     const unsigned k = cell_key(a, mol, ci[0], ci[1], ci[2]);
     a.key[g] = (int)k;
     a.wpos[g] = make_float4(pw[0], pw[1], pw[2], __int_as_float(mol));
@@ -307,10 +319,7 @@ __device__ void list_one_bead(const KArgs<Real>& a, int64_t t, unsigned& fl) {
               sc[c] = (int)s;
             }
           const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-          float rl2;
-          if ((g ^ j) & 1) rl2 = a.c.rl_cr2;
-          else if (st_g && ((jw >> NBR_J_BITS) & 1)) rl2 = a.c.rl_ss2;
-          else continue;
+          const float rl2 = list_r2(a.c, ((g ^ j) & 1) != 0, st_g && ((jw >> NBR_J_BITS) & 1));
           if (r2 >= rl2) continue;
           if (a.n_mol > 1 && __float_as_int(a.wpos[j].w) != mol) continue;
           const int ent = ent_make(j, sc[0], sc[1], sc[2]);
@@ -346,10 +355,7 @@ __device__ __forceinline__ void consider(const KArgs<Real>& a, const float* p, i
       sc[c] = (int)s;
     }
   const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  float rl2;
-  if ((g ^ j) & 1) rl2 = a.c.rl_cr2;
-  else if (st_g && ((jw >> NBR_J_BITS) & 1)) rl2 = a.c.rl_ss2;
-  else return;
+  const float rl2 = list_r2(a.c, ((g ^ j) & 1) != 0, st_g && ((jw >> NBR_J_BITS) & 1));
   if (r2 >= rl2) return;
   if (a.n_mol > 1 && __float_as_int(a.wpos[j].w) != mol) return;
   const int ent = ent_make(j, sc[0], sc[1], sc[2]);
@@ -382,10 +388,8 @@ __device__ __forceinline__ int pair_entry(const KArgs<Real>& a, float4 me, float
   const int gw = __float_as_int(me.w), jw = __float_as_int(o.w);
   const int g = gw & JMASK, j = jw & JMASK;
   if (j == g) return -1;
-  float rl2;
-  if ((g ^ j) & 1) rl2 = a.c.rl_cr2;
-  else if (((gw & jw) >> NBR_J_BITS) & 1) rl2 = a.c.rl_ss2;
-  else return -1;
+  const float rl2 = list_r2(a.c, ((g ^ j) & 1) != 0, ((gw & jw) >> NBR_J_BITS) & 1);
+  if (rl2 < 0.0f) return -1;
   float d[3] = {o.x - me.x, o.y - me.y, o.z - me.z};
   int sc[3] = {0, 0, 0};
   if (a.periodic) {
@@ -618,7 +622,7 @@ __device__ void rebuild_list_lanes(const KArgs<Real>& a, unsigned& fl, int* list
         const int jw = __float_as_int(o.w), j = jw & JMASK;
         const float dx = o.x - px, dy = o.y - py, dz = o.z - pz;
         const float r2 = dx * dx + dy * dy + dz * dz;
-        const float rl2 = ((g ^ j) & 1) ? a.c.rl_cr2 : ((st_g && ((jw >> NBR_J_BITS) & 1)) ? a.c.rl_ss2 : -1.0f);
+        const float rl2 = list_r2(a.c, ((g ^ j) & 1) != 0, st_g && ((jw >> NBR_J_BITS) & 1));
         if (r2 < rl2 && j != g && (a.n_mol == 1 || __float_as_int(a.wpos[j].w) == mol)) {
           ++total;
           if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed
@@ -698,7 +702,7 @@ __device__ void rebuild_list_lanes_hash(const KArgs<Real>& a, unsigned& fl, int*
           const int jw = __float_as_int(o.w), j = jw & JMASK;
           const float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
           const float r2 = dx * dx + dy * dy + dz * dz;
-          const float rl2 = ((g ^ j) & 1) ? a.c.rl_cr2 : ((st_g && ((jw >> NBR_J_BITS) & 1)) ? a.c.rl_ss2 : -1.0f);
+          const float rl2 = list_r2(a.c, ((g ^ j) & 1) != 0, st_g && ((jw >> NBR_J_BITS) & 1));
           if (r2 < rl2 && j != g && (a.n_mol == 1 || __float_as_int(a.wpos[j].w) == mol)) {
             ++total;
             if (cnt < a.cap) {   // insertion by partner slot keeps the force sum order fixed

@@ -142,7 +142,7 @@ def main():
     a = ap.parse_args()
     import torch
     torch.cuda.init()
-    ov = {k: float(v) for k, v in (x.split("=", 1) for x in a.param)}
+    ov = {k: (int(v) if v.lstrip("-").isdigit() else float(v)) for k, v in (x.split("=", 1) for x in a.param)}
     r = measure(a.n_mol, a.n_bp, a.equil, a.every, a.samples, a.seed, init_lp=a.init_lp, overrides=ov)
     short = {k: v for k, v in r.items() if not k.endswith("correlator")}
     print(json.dumps(short))
