@@ -81,7 +81,7 @@ def build_workload(name: str, seed: int = 0, n_bp: int = 1_000_000):
 # kernel from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
 # the bench's multi-step launches on the 1 Mbp confined workload), keyed by a
 # hash of the kernel sources it was taken on: a changed kernel reports no traffic.
-ENGINE_TRAFFIC = {("dca68512036919e4", "c3rows"): 211.9}   # 1 Mbp confined rows, skin 0.3
+ENGINE_TRAFFIC = {("6acec291ae9a864b", "c3"): 222.4}   # 1 Mbp confined walk, skin 0.3, 1.70 partners
 ENGINE_SOURCES = ("engine.cuh", "engine_kernels.cuh", "kern_mixed.cu")   # the step kernel's code
 
 
@@ -532,6 +532,8 @@ def main():
     traffic = engine_traffic_per_nt_step(prec, args.workload)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": None if traffic is None else traffic * cfg.n_nt * steps_per_launch,
+            "traffic_capture": None if traffic is None else
+            f"{traffic} B per nucleotide-step from ncu at skin 0.3, scaled by nucleotide-steps per launch",
             "peak_kind": peak_kind, "bytes_per_nt_step": b_nt, "neighbors_per_bead": nbar,
             "algorithmic_bytes_per_launch": per_launch_bytes, "steps_per_launch": steps_per_launch,
             "launch_ms": launch_s * 1e3, "launches_timed": prof["engine_launches"],
