@@ -208,7 +208,8 @@ static void host_maxwell(const dsdna_params& p, int mol, int N, const double* u,
 // staging layout: four [cnt][3] FP64 regions X, V, u, Om -- the callers' own
 // layout, so each array moves in one copy
 __global__ void k_scatter_state(const double* stage, int64_t g0, int64_t cnt, unsigned mask, int fp64, int cur, int64_t n,
-                                double* X, double* V, void* Om, int4* Kw, float4* U, double* ud, const int* topo) {
+                                double* X, double* V, void* Om, int4* Kw, float4* U, double* ud, const int* topo,
+                                double S0, double S1, double S2) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cnt) return;
   const int64_t g = g0 + i;
@@ -242,7 +243,7 @@ __global__ void k_scatter_state(const double* stage, int64_t g0, int64_t cnt, un
   }
   if (!fp64 && (mask & 1)) {
     int4 k = Kw[(size_t)cur * n + g];
-    k.x = fix32(Xc[g]); k.y = fix32(Xc[n + g]); k.z = fix32(Xc[2 * n + g]);
+    k.x = fixs(Xc[g], S0); k.y = fixs(Xc[n + g], S1); k.z = fixs(Xc[2 * n + g], S2);
     Kw[(size_t)cur * n + g] = k;
   }
 }
@@ -333,7 +334,7 @@ static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
     a.cellh[k] = (float)(a.periodic ? c->p.box[k] / c->nc[k] : c->cellh);
     a.invcellh[k] = 1.0f / a.cellh[k];
     a.invLf[k] = a.periodic ? (float)(1.0 / a.L[k]) : 0.0f;
-    a.Lfix[k] = (uint32_t)(uint64_t)llround(a.L[k] * 536870912.0);
+    mirror_scale(a, k);
   }
   a.mol_off = c->mol_off; a.ext = c->ext_d;
   a.bar = c->bar; a.err = c->err; a.step = c->step_d; a.rebuild = c->rebuild; a.nrebuild = c->nrebuild;
@@ -389,7 +390,8 @@ static int upload_state(dsdna_ctx* c, int64_t g0, int64_t cnt, const double* X, 
          "upload state");
   const int cur = (int)(c->step & 1);
   k_scatter_state<<<(unsigned)((cnt + 255) / 256), 256, 0, c->st>>>(c->stage, g0, cnt, mask, c->fp64(), cur, c->ns, c->X,
-                                                                     c->V, c->Om, c->Kw, c->U, c->ud, c->topo);
+                                                                     c->V, c->Om, c->Kw, c->U, c->ud, c->topo,
+                                                                     c->kf.fixS[0], c->kf.fixS[1], c->kf.fixS[2]);
   CK(cudaGetLastError(), "scatter state");
   CK(cudaStreamSynchronize(c->st), "upload state sync");
   return DSDNA_OK;

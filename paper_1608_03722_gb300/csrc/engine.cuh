@@ -12,9 +12,14 @@
 // Precision (Real = float, "mixed"): the FP64 centre positions X and
 // velocities V are the integrator's accumulators; forces, orientation u and
 // angular velocity are FP32.  Displacements between nucleotides come from a
-// fixed-point mirror of X (low 32 bits of round(X * 2^29)): the difference of
-// two mirrors is exact for separations below 4 nm, so no FP64 subtraction is
-// needed in the force loops.  Real = double runs every step in FP64.
+// fixed-point mirror of X: the low 32 bits of round(X S) per axis.  In a
+// periodic box 2^32 grid units span L / k (k = max(1, floor(L / 8 nm))), so
+// the mirror is the same for every periodic image of a position and the
+// wrap-around difference of two mirrors is their minimum-image separation
+// (below L / 2k, at least 4 nm), with no image bookkeeping; in an open box
+// S = 2^29 / nm (separations below 4 nm).  The grid unit stays at or below
+// 3.7e-9 nm.
+// Real = double runs every step in FP64.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,8 +50,6 @@ constexpr int MODE_EXT = 4;   // launch flag: kernel instance with circular mole
 constexpr int MODE_FUSED = 8; // launch flag (MODE_STEP): instance that rebuilds the list in the kernel
 constexpr int NTERMS = 10;
 constexpr int EOUT_STRIDE = 16;           // energy terms + 6 virial
-constexpr float FIX_SCALE_F = 1.0f / 536870912.0f;  // 2^-29
-constexpr double FIX_SCALE_D = 1.0 / 536870912.0;
 constexpr int NBR_J_BITS = 27;   // slot field of a cell-sorted bead word (bit 27: steric flag)
 
 // Neighbour-list entry: partner slot j in the low ENT_J_BITS bits, then the
@@ -139,7 +142,9 @@ struct KArgs {
   float Lf[3];
   float invLf[3];
   double L[3];
-  unsigned Lfix[3];
+  double fixS[3];   // fixed-point mirror: grid units per nm (2^32 / L periodic, 2^29 open)
+  float fixSf[3];   // the same in FP32
+  float fixq[3];    // nm per grid unit
   // molecules
   const int64_t* mol_off;  // [n_mol + 1] base-pair offsets
   const double* ext;       // [n_mol][8]: f xyz, torque xyz
@@ -157,6 +162,19 @@ struct KArgs {
   int use_cond;
   cudaGraphConditionalHandle h_while;
 };
+
+// Mirror grid of axis k (a.periodic and a.L set): 2^32 units per L / m with
+// m = max(1, floor(L / 8 nm)) in a periodic box, so that 32-bit wrap-around
+// differences are minimum-image separations, or 2^29 units per nm in an
+// open box.
+template <class Real>
+inline void mirror_scale(KArgs<Real>& a, int k) {
+  const double m = a.periodic ? (a.L[k] >= 16.0 ? (double)(int64_t)(a.L[k] / 8.0) : 1.0) : 1.0;
+  const double S = a.periodic ? 4294967296.0 * m / a.L[k] : 536870912.0;
+  a.fixS[k] = S;
+  a.fixSf[k] = (float)S;
+  a.fixq[k] = (float)(1.0 / S);
+}
 
 // ---------------------------------------------------------------- small vectors
 template <class R>
@@ -253,24 +271,27 @@ template <class Real> struct SPos;
 template <> struct SPos<float> { int kx, ky, kz; float ux, uy, uz; };
 template <> struct SPos<double> { double x, y, z, ux, uy, uz; };
 
-__device__ __forceinline__ float fixdiff(int a, int b) {   // (b - a) in nm, exact wrap-around difference
-  return (float)(int)((unsigned)b - (unsigned)a) * FIX_SCALE_F;
+// Separation b - o of two staged slots: wrap-around difference of the mirrors
+// times the grid unit q (per axis); FP64 slots subtract their positions.
+__device__ __forceinline__ V3<float> rel(const SPos<float>& o, const SPos<float>& b, const float* q) {
+  return V3<float>{(float)(int)((unsigned)b.kx - (unsigned)o.kx) * q[0],
+                   (float)(int)((unsigned)b.ky - (unsigned)o.ky) * q[1],
+                   (float)(int)((unsigned)b.kz - (unsigned)o.kz) * q[2]};
 }
-__device__ __forceinline__ V3<float> rel(const SPos<float>& o, const SPos<float>& b) {
-  return V3<float>{fixdiff(o.kx, b.kx), fixdiff(o.ky, b.ky), fixdiff(o.kz, b.kz)};
-}
-__device__ __forceinline__ V3<double> rel(const SPos<double>& o, const SPos<double>& b) {
+__device__ __forceinline__ V3<double> rel(const SPos<double>& o, const SPos<double>& b, const float* /*q*/) {
   return V3<double>{b.x - o.x, b.y - o.y, b.z - o.z};
 }
 template <class Real> __device__ __forceinline__ V3<Real> uvec(const SPos<Real>& s) { return V3<Real>{s.ux, s.uy, s.uz}; }
 
-// Low 32 bits of round(x * 2^29) (ties away from zero), from the bits of x
-// with integer operations only: the FP64 pipe of GB300 runs at a small
-// fraction of the integer rate.  Valid for |x| < 2^33 nm.
-__device__ __forceinline__ int fix32(double x) {
-  const long long b = __double_as_longlong(x);
-  const int sh = 1046 - (int)((b >> 52) & 0x7FF);          // right shift of the 53-bit significand
-  if (sh > 53) return 0;                                    // |x| < 2^-30 rounds to zero
+// Mirror coordinate: low 32 bits of round(x S) (ties away from zero).  One
+// FP64 multiply, then the rounding by integer operations on the bits of the
+// product (the FP64 pipe of GB300 runs at a small fraction of the integer
+// rate); exact for any |x S| below 2^63.
+__device__ __forceinline__ int fixs(double x, double S) {
+  const long long b = __double_as_longlong(x * S);
+  const int sh = 1075 - (int)((b >> 52) & 0x7FF);          // right shift of the 53-bit significand
+  if (sh > 53) return 0;                                    // |x S| < 1/2 rounds to zero
+  if (sh < -40) return 0;                                   // an integer multiple of 2^32
   const unsigned long long m = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
   const unsigned long long r = sh > 0 ? (m + (1ull << (sh - 1))) >> sh : m << (-sh);
   const unsigned lo = (unsigned)r;
@@ -299,8 +320,8 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)((((unsigned long long)a << 29) + 0x3800000000000000ull) | sign));
 }
 
-// bead offset -h u on the fixed-point grid (rebuild trigger only)
-__device__ __forceinline__ int bead_off(float hu) { return __float2int_rn(-hu * 536870912.0f); }
+// bead offset -h u on the fixed-point grid (rebuild trigger only); Sf: grid units per nm
+__device__ __forceinline__ int bead_off(float hu, float Sf) { return __float2int_rn(-hu * Sf); }
 
 template <class Real>
 __device__ __forceinline__ void load_slot(const KArgs<Real>& a, int cur, int64_t g, SPos<Real>& s) {

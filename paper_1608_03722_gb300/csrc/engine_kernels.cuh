@@ -72,7 +72,7 @@ __device__ __forceinline__ void mark_open(const KArgs<Real>& a, const SegSmem<Re
   const int fa = sm.flg[ra];
   if (fa == 0) return;
   const SPos<Real> pa = sm.pos[ra], pb = sm.pos[rb];
-  const V3<Real> d = rel(pa, pb) + a.c.h * (uvec(pb) - uvec(pa));
+  const V3<Real> d = rel(pa, pb, a.fixq) + a.c.h * (uvec(pb) - uvec(pa));
   if (dot(d, d) > a.c.rchb2) sm.flg[ra] = fa | F_OPEN;
 }
 __device__ __forceinline__ bool bp_open(const int* flg, int64_t k, int mol) {
@@ -118,7 +118,7 @@ struct GlobalSrc {
   __device__ __forceinline__ bool open(int64_t k, int /*mol*/) const {
     k = wrap(k);
     const SPos<Real> pa = pos(2 * k), pb = pos(2 * k + 1);
-    const V3<Real> d = rel(pa, pb) + a.c.h * (uvec(pb) - uvec(pa));
+    const V3<Real> d = rel(pa, pb, a.fixq) + a.c.h * (uvec(pb) - uvec(pa));
     return dot(d, d) > a.c.rchb2;
   }
 };
@@ -159,7 +159,7 @@ __device__ __forceinline__ void owner_eval(const KArgs<Real>& a, const Src& src,
   const SPos<Real> sq = src.pos(src.step(o, dir));
   const Real h = a.c.h;
   const V3<Real> uo = uvec(so), uq = uvec(sq);
-  const V3<Real> Rq = rel(so, sq);
+  const V3<Real> Rq = rel(so, sq, a.fixq);
   const V3<Real> bo = -h * uo, po = h * uo, bq = Rq - h * uq, pq = Rq + h * uq;
   // FENE + WCA, Morse
   V3<Real> fb = t_fene(a.c, bq - bo, fl, E);
@@ -181,7 +181,7 @@ __device__ __forceinline__ void owner_eval(const KArgs<Real>& a, const Src& src,
   if (W) { vir_add(W, po, f1); vir_add(W, bq, f2); vir_add(W, pq, -(f1 + f2)); }
   if ((f & F_PREV) && !skip_bend) {
     const SPos<Real> sr = src.pos(src.step(o, -dir));
-    const V3<Real> pr = rel(so, sr) + h * uvec(sr);
+    const V3<Real> pr = rel(so, sr, a.fixq) + h * uvec(sr);
     V3<Real> g1, g2;
     t_bend(a.c, pr - po, pq - po, g1, g2, E);
     out.pp += g1; out.np += g2; out.sp -= (g1 + g2);
@@ -336,12 +336,11 @@ __device__ __forceinline__ void store_state(const KArgs<Real>& a, int nxt, int64
   }
 }
 
-// Own periodic image word of slot gu (image fields and steric flag): in mixed
-// precision the fourth word of the mirror (staged a tile ago and still
-// cached); the FP64 path keeps it apart.
+// Own periodic image word of slot gu (image fields and steric flag) in the
+// FP64 path; the mixed path's mirror needs no image.
 template <class Real>
 __device__ __forceinline__ int own_image(const KArgs<Real>& a, int cur, unsigned gu) {
-  if constexpr (sizeof(Real) == 4) return a.Kw[(unsigned)cur * (unsigned)a.ns + gu].w;
+  if constexpr (sizeof(Real) == 4) return 0;
   else return a.img[gu];
 }
 
@@ -362,15 +361,10 @@ __device__ __forceinline__ V3<Real> pair_force(const KArgs<Real>& a, int cur, un
     const float4 u4 = a.U[(unsigned)cur * ns + (unsigned)j];
     wj = kj.w;
     uj = V3<float>{u4.x, u4.y, u4.z};
-    unsigned dx = (unsigned)kj.x - (unsigned)me.kx, dy = (unsigned)kj.y - (unsigned)me.ky,
-             dz = (unsigned)kj.z - (unsigned)me.kz;
-    if (a.periodic) {
-      const int mx = img_comp(img_me, 0) - img_comp(kj.w, 0) + ent_shift(ent, 0);
-      const int my = img_comp(img_me, 1) - img_comp(kj.w, 1) + ent_shift(ent, 1);
-      const int mz = img_comp(img_me, 2) - img_comp(kj.w, 2) + ent_shift(ent, 2);
-      dx += (unsigned)mx * a.Lfix[0]; dy += (unsigned)my * a.Lfix[1]; dz += (unsigned)mz * a.Lfix[2];
-    }
-    R = V3<float>{(float)(int)dx * FIX_SCALE_F, (float)(int)dy * FIX_SCALE_F, (float)(int)dz * FIX_SCALE_F};
+    // the mirrors' wrap-around difference is the minimum-image separation
+    R = V3<float>{(float)(int)((unsigned)kj.x - (unsigned)me.kx) * a.fixq[0],
+                  (float)(int)((unsigned)kj.y - (unsigned)me.ky) * a.fixq[1],
+                  (float)(int)((unsigned)kj.z - (unsigned)me.kz) * a.fixq[2]};
   } else {
     const double* X = a.X + (size_t)cur * 3 * a.ns;
     const double* ud = a.ud + (size_t)cur * 3 * a.ns;
@@ -442,7 +436,7 @@ __device__ __forceinline__ void warp_pairs(const KArgs<Real>& a, const SegSmem<R
         const int rL = ring(B + L);
         const int fL = sm.flg[rL];
         const SPos<Real>& mL = sm.pos[rL];
-        const int img = a.periodic ? own_image(a, cur, gL) : 0;
+        const int img = (sizeof(Real) == 8 && a.periodic) ? own_image(a, cur, gL) : 0;
         const int ent = a.nbr[(unsigned)(p - sm.pst[L]) * ns + gL];
         const V3<Real> fw = pair_force(a, cur, gL, mL, uvec(mL), fL, img, ent, (V3<Real>*)nullptr, (Real*)nullptr);
         Real* o = sm.pf + 3 * (k * SEG + lane);
@@ -500,7 +494,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
     // hydrogen bond with the partner (App. A Eq. 10), broken beyond rc
     {
       const SPos<Real>& q = sm.pos[ring(g ^ 1)];
-      const V3<Real> d = rel(me, q) + h * uvec(q) - h * um;   // patch_q - patch_me
+      const V3<Real> d = rel(me, q, a.fixq) + h * uvec(q) - h * um;   // patch_q - patch_me
       const Real r2 = dot(d, d);
       if (r2 <= a.c.rchb2) {
         const Real khb = (f & F_GC) ? a.c.khb_gc : a.c.khb;   // Sec. 5: A.T / G.C stiffness
@@ -523,7 +517,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
     if constexpr (MODE == MODE_ENERGY) {
       if (act) {
         const int nn = a.ncnt[gu];
-        const int img_me = a.periodic ? own_image(a, cur, gu) : 0;
+        const int img_me = (sizeof(Real) == 8 && a.periodic) ? own_image(a, cur, gu) : 0;
         for (int q = 0; q < nn; ++q) {
           V3<Real> d;
           Real e;
@@ -547,7 +541,7 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
       const Real tn2 = dot(Tq, Tq);
       if (tn2 > (Real)0) {
         const V3<Real> th = rsqrt_(tn2) * Tq;
-        V3<Real> rho = (Real)-0.5 * rel(me, sm.pos[ring(g ^ 1)]);   // centre offset from the pair centre
+        V3<Real> rho = (Real)-0.5 * rel(me, sm.pos[ring(g ^ 1)], a.fixq);   // centre offset from the pair centre
         rho -= dot(rho, th) * th;
         const Real S = (Real)2 * dot(rho, rho);
         if (S > (Real)1e-12) Fe += ((Real)1 / S) * cross(Tq, rho);
@@ -636,13 +630,14 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
             a.X[gu] = Xd[0]; a.X[ns + gu] = Xd[1]; a.X[2 * ns + gu] = Xd[2];
           }
         }
-        const int k0 = fix32(Xd[0]), k1 = fix32(Xd[1]), k2 = fix32(Xd[2]);
+        // the new position's mirror (in the FP64 path it serves the rebuild trigger only)
+        const int k0 = fixs(Xd[0], a.fixS[0]), k1 = fixs(Xd[1], a.fixS[1]), k2 = fixs(Xd[2], a.fixS[2]);
         store_state(a, nxt, g, k0, k1, k2, Xd, un, packed);
         // rebuild trigger: a bead moved more than skin/2 since the last build
         const float hf = (float)h;
-        const float ddx = fixdiff(kr[0], k0 + bead_off(hf * (float)un.x));
-        const float ddy = fixdiff(kr[1], k1 + bead_off(hf * (float)un.y));
-        const float ddz = fixdiff(kr[2], k2 + bead_off(hf * (float)un.z));
+        const float ddx = (float)(int)((unsigned)(k0 + bead_off(hf * (float)un.x, a.fixSf[0])) - (unsigned)kr[0]) * a.fixq[0];
+        const float ddy = (float)(int)((unsigned)(k1 + bead_off(hf * (float)un.y, a.fixSf[1])) - (unsigned)kr[1]) * a.fixq[1];
+        const float ddz = (float)(int)((unsigned)(k2 + bead_off(hf * (float)un.z, a.fixSf[2])) - (unsigned)kr[2]) * a.fixq[2];
         if (ddx * ddx + ddy * ddy + ddz * ddz > a.c.skin_half2) fl |= B_STALE;
       }
     }

@@ -106,7 +106,8 @@ int setup_device(int dev, DeviceSetup** out) {
 // Sec. 2 (no anchored or loaded base pairs), SoA centres, fixed-point mirror,
 // FP32 orientation; zero the cell counts' companions and the control words.
 __global__ void k_noalloc_prep(const double* X, const double* u, int64_t n, int64_t ns, int n_mol, const int64_t* mol_off,
-                               int steric_phase, double* Xs, int4* Kw, float4* U, int* topo, unsigned* ctrl) {
+                               int steric_phase, double* Xs, int4* Kw, float4* U, int* topo, unsigned* ctrl, double S0,
+                               double S1, double S2) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g == 0) {
     ctrl[0] = 0u;                                   // error word
@@ -133,7 +134,7 @@ __global__ void k_noalloc_prep(const double* X, const double* u, int64_t n, int6
   topo[g] = f | (m << MOL_SHIFT);
   const double x0 = X[3 * g], x1 = X[3 * g + 1], x2 = X[3 * g + 2];
   Xs[g] = x0; Xs[ns + g] = x1; Xs[2 * ns + g] = x2;
-  Kw[g] = make_int4(fix32(x0), fix32(x1), fix32(x2), 0);
+  Kw[g] = make_int4(fixs(x0, S0), fixs(x1, S1), fixs(x2, S2), 0);
   double u0 = u[3 * g], u1 = u[3 * g + 1], u2 = u[3 * g + 2];
   const double l2 = u0 * u0 + u1 * u1 + u2 * u2;
   if (fabs(l2 - 1.0) > 1e-6) { const double l = sqrt(l2); u0 /= l; u1 /= l; u2 /= l; }
@@ -242,7 +243,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
     a.cellh[k] = (float)(periodic ? p->box[k] / nc[k] : cellh);
     a.invcellh[k] = 1.0f / a.cellh[k];
     a.invLf[k] = periodic ? (float)(1.0 / a.L[k]) : 0.0f;
-    a.Lfix[k] = (uint32_t)(uint64_t)llround(a.L[k] * 536870912.0);
+    mirror_scale(a, k);
   }
   a.mol_off = reinterpret_cast<int64_t*>(b + O_MOLOFF);
   a.ext = reinterpret_cast<double*>(b + O_EXT);
@@ -263,7 +264,7 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   if (e == cudaSuccess) e = cudaMemsetAsync(a.ncnt, 0, sizeof(int) * n, st);
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
   k_noalloc_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, u, n, NA_MAX_NT, n_mol, a.mol_off, p->steric_phase, a.X, a.Kw, a.U,
-                                                               a.topo, ctrl);
+                                                               a.topo, ctrl, a.fixS[0], a.fixS[1], a.fixS[2]);
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(DSDNA_ECUDA, cudaGetErrorString(e));
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(s->grid, (n + NA_T - 1) / NA_T));

@@ -135,15 +135,16 @@ __device__ void rebuild_bin(const KArgs<Real>& a, int cur, unsigned& fl) {
     if constexpr (sizeof(Real) == 4) {
       int4 kw = a.Kw[(size_t)cur * a.ns + g];
       const float4 u = a.U[(size_t)cur * a.ns + g];
-      a.kref[g] = kw.x + bead_off(h * u.x);
-      a.kref[a.ns + g] = kw.y + bead_off(h * u.y);
-      a.kref[2 * a.ns + g] = kw.z + bead_off(h * u.z);
+      a.kref[g] = kw.x + bead_off(h * u.x, a.fixSf[0]);
+      a.kref[a.ns + g] = kw.y + bead_off(h * u.y, a.fixSf[1]);
+      a.kref[2 * a.ns + g] = kw.z + bead_off(h * u.z, a.fixSf[2]);
       kw.w = packed;
       a.Kw[(size_t)cur * a.ns + g] = kw;
     } else {
       const double* X = a.X + (size_t)cur * 3 * a.ns;
       const double* u = a.ud + (size_t)cur * 3 * a.ns;
-      for (int c = 0; c < 3; ++c) a.kref[c * a.ns + g] = fix32(X[c * a.ns + g]) + bead_off(h * (float)u[c * a.ns + g]);
+      for (int c = 0; c < 3; ++c)
+        a.kref[c * a.ns + g] = fixs(X[c * a.ns + g], a.fixS[c]) + bead_off(h * (float)u[c * a.ns + g], a.fixSf[c]);
     }
   }
 }
