@@ -511,17 +511,24 @@ def main():
         pr = ctx.step_profiled(S)
         for k in prof:
             prof[k] += pr[k]
-    # neighbours per bead (full list), for the algorithmic byte count
-    nbar = 2.0 * len(ctx.neighbor_pairs()) / cfg.n_nt
+    # neighbours per bead (full list), for the algorithmic byte count; under pair
+    # halving a pair within one 32-slot tile is evaluated once, one across tiles twice
+    pairs = ctx.neighbor_pairs()
+    nbar = 2.0 * len(pairs) / cfg.n_nt
+    halved = ctx.info()["halved_tiles"] > 0
+    same_tile = int(np.count_nonzero((pairs[:, 0] >> 5) == (pairs[:, 1] >> 5))) if len(pairs) else 0
+    ebar = (2.0 * len(pairs) - same_tile) / cfg.n_nt
 
     # algorithmic bytes per nucleotide-step of the fused force + Langevin kernel:
     # mixed: read X, V (FP64 24 + 24), Omega (FP32 12), kref 12, mirror (its fourth word
-    # carries the periodic image) + orientation (16 + 16), topology 4, count 4, list 4 n;
-    # write X, V, Omega, next mirror + orientation (24 + 24 + 12 + 16 + 16).  FP64: X, u,
-    # V, Omega 24 each read and written, kref 12, topology, count, image (periodic) 4 each.
+    # is the image word) + orientation (16 + 16), topology 4, count 4, and the list: 4 n
+    # entries, or under pair halving 8 bytes of entry codes, the tile's evaluated pairs
+    # (4 e per nucleotide) and its pair count (4 per 32); write X, V, Omega, next mirror
+    # + orientation (24 + 24 + 12 + 16 + 16).  FP64: X, u, V, Omega 24 each read and
+    # written, kref 12, topology, count, image (periodic) 4 each.
     periodic = 1 if cfg.box[0] > 0 else 0
     if prec == D.PREC_MIXED:
-        b_nt = 112 + 92 + 4 * nbar
+        b_nt = 112 + 92 + (8 + 4 * ebar + 4.0 / 32 if halved else 4 * nbar)
     else:
         b_nt = (96 + 12 + 8 + 4 * periodic) + 96 + 4 * nbar
     steps_per_launch = prof["steps"] / max(prof["engine_launches"], 1)
@@ -535,6 +542,7 @@ def main():
             "traffic_capture": None if traffic is None else
             f"{traffic} B per nucleotide-step from ncu at skin 0.3, scaled by nucleotide-steps per launch",
             "peak_kind": peak_kind, "bytes_per_nt_step": b_nt, "neighbors_per_bead": nbar,
+            "pair_halving": halved, "evaluated_pairs_per_nucleotide": ebar if halved else nbar,
             "algorithmic_bytes_per_launch": per_launch_bytes, "steps_per_launch": steps_per_launch,
             "launch_ms": launch_s * 1e3, "launches_timed": prof["engine_launches"],
             "rebuild_ms_per_rebuild": prof["rebuild_ms"] / max(prof["rebuild_launches"], 1),

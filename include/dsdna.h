@@ -151,6 +151,13 @@ typedef struct dsdna_params {
    * size, the reading whose torsional persistence length matches Sec. 3.2);
    * <= 0 gives such pairs sigma_cross like every other cross-strand pair. */
   double sigma_cross_steric;
+  /* Mixed precision, list rebuilt by separate kernels (rebuild_mode 1, or 0
+   * above DSDNA_FUSED_REBUILD_MAX_NT): 1 evaluates a list pair whose two
+   * nucleotides share a 32-slot tile of the step kernel once and gives the
+   * other nucleotide its negative (Newton's third law); 0 evaluates every
+   * list pair from both sides.  The pair force is antisymmetric bit for bit,
+   * so both give the same forces and trajectories bit for bit. */
+  int pair_halving;
 } dsdna_params;
 
 /* Molecules and (optional) initial state.  NULL X/u builds ideal relaxed
@@ -208,6 +215,8 @@ typedef struct dsdna_info {
   int64_t device_bytes;  /* bytes allocated on the device */
   int64_t engine_launches; /* persistent step/force/energy kernel launches so far */
   int rebuild_in_step;   /* 1: the step kernel rebuilds the list itself (rebuild_mode) */
+  int64_t halved_tiles;  /* 32-slot tiles whose same-tile list pairs the last build set to be evaluated
+                            once (pair_halving); 0 when pair halving is off */
 } dsdna_info;
 
 /* Per-launch timing of dsdna_step_profiled (CUDA events on the context stream). */

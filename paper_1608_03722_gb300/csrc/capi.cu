@@ -51,6 +51,7 @@ struct dsdna_ctx {
   double* X = nullptr; double* V = nullptr; void* Om = nullptr;
   int4* Kw = nullptr; float4* U = nullptr; double* ud = nullptr;
   int* topo = nullptr; int* img = nullptr; int* kref = nullptr; int* nbr = nullptr; int* ncnt = nullptr;
+  int* evl = nullptr; uint2* psrc = nullptr; int* tcnt = nullptr;   // pair halving (mixed precision)
   int64_t n_junc = 0;            // junction owners of circular molecules (8 per ring)
   bool fused = false;            // list rebuilt inside the step kernel
   // kernel instance: with circular molecules or the bubble rule, MODE_EXT;
@@ -324,6 +325,7 @@ static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
   a.spin_budget = 4000000000ull;
   a.X = c->X; a.V = c->V; a.Om = (Real*)c->Om; a.Kw = c->Kw; a.U = c->U; a.ud = c->ud;
   a.topo = c->topo; a.img = c->img; a.kref = c->kref; a.nbr = c->nbr; a.ncnt = c->ncnt;
+  a.evl = sizeof(Real) == 4 ? c->evl : nullptr; a.psrc = c->psrc; a.tcnt = c->tcnt;
   a.cnt = c->cnt; a.start = c->start; a.H = c->H; a.table = c->table; a.morton_bits = c->morton_bits; a.key = c->key;
   a.cent = c->cent; a.wpos = c->wpos; a.bsum = c->bsum;
   a.periodic = c->p.box[0] > 0.0 ? 1 : 0;
@@ -359,6 +361,7 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
   if (p->precision != DSDNA_PREC_MIXED && p->precision != DSDNA_PREC_FP64) return fail(nullptr, DSDNA_EINVAL, "precision");
   if (p->bubble_rule < 0 || p->bubble_rule > 2) return fail(nullptr, DSDNA_EINVAL, "bubble_rule must be 0, 1 or 2");
   if (p->rebuild_mode < 0 || p->rebuild_mode > 2) return fail(nullptr, DSDNA_EINVAL, "rebuild_mode must be 0, 1 or 2");
+  if (p->pair_halving < 0 || p->pair_halving > 1) return fail(nullptr, DSDNA_EINVAL, "pair_halving must be 0 or 1");
   if (p->K2_gc < 0.0) return fail(nullptr, DSDNA_EINVAL, "K2_gc must be >= 0");
   if (p->noise < 0 || p->noise > 2) return fail(nullptr, DSDNA_EINVAL, "noise mode");
   if (p->steric_phase < 0 || p->steric_phase > 2) return fail(nullptr, DSDNA_EINVAL, "steric_phase must be 0, 1 or 2");
@@ -412,6 +415,7 @@ extern "C" void dsdna_default_params(dsdna_params* p) {
   p->seed = 0; p->noise = DSDNA_NOISE_UNIFORM; p->steric_phase = 0;
   p->skin = 0.3; p->precision = DSDNA_PREC_MIXED;
   p->sigma_cross_steric = 1.0;   // Sec. 2, reading A1: two steric beads at sigma = 1 on either strand
+  p->pair_halving = 1;
 }
 
 extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys, const dsdna_allocator* alloc,
@@ -513,6 +517,11 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
     if (!c->jout) return bad(fail(c, DSDNA_ENOMEM, "device allocation failed: jout"));
   }
   ALLOC(nbr, int, (size_t)c->p.max_neighbors * ns); ALLOC(ncnt, int, ns);
+  // pair halving: mixed precision with the list rebuilt by the separate kernels
+  if (!f64 && c->p.pair_halving && !c->fused) {
+    const size_t nt = (nn + SEG_SLOTS - 1) / SEG_SLOTS;
+    ALLOC(evl, int, nt * EVL_CAP); ALLOC(psrc, uint2, ns); ALLOC(tcnt, int, nt);
+  }
   ALLOC(cnt, unsigned, c->H); ALLOC(start, unsigned, (size_t)c->H + 1); ALLOC(key, int, nn);
   ALLOC(cent, float4, nn); ALLOC(wpos, float4, nn);
   ALLOC(mol_off, int64_t, c->n_mol + 1); ALLOC(ext_d, double, (size_t)c->n_mol * 8);
@@ -1116,6 +1125,11 @@ extern "C" int dsdna_get_info(const dsdna_ctx* c, dsdna_info* info) {
   info->skin = c->p.skin;
   info->cell_table = c->H;
   info->device_bytes = c->bytes;
+  if (c->tcnt && info->rebuilds > 0) {
+    std::vector<int> tc((size_t)((c->n + SEG_SLOTS - 1) / SEG_SLOTS));
+    if (cudaMemcpy(tc.data(), c->tcnt, sizeof(int) * tc.size(), cudaMemcpyDeviceToHost) == cudaSuccess)
+      for (int v : tc) info->halved_tiles += v >= 0 ? 1 : 0;
+  }
   return DSDNA_OK;
 }
 

@@ -51,6 +51,8 @@ constexpr int MODE_FUSED = 8; // launch flag (MODE_STEP): instance that rebuilds
 constexpr int NTERMS = 10;
 constexpr int EOUT_STRIDE = 16;           // energy terms + 6 virial
 constexpr int NBR_J_BITS = 27;   // slot field of a cell-sorted bead word (bit 27: steric flag)
+constexpr int EVL_CAP = 96;      // evaluated pairs per tile under pair halving (else the tile's whole list)
+constexpr int HALF_NMAX = 8;     // longest list a tile under pair halving may hold
 
 // Neighbour-list entry: partner slot j in the low ENT_J_BITS bits, then the
 // minimum-image shift s + 1 in {0, 1, 2} of each axis in a 2-bit field
@@ -120,6 +122,11 @@ struct KArgs {
   int* kref;       // [3][n] mirror at the last build
   int* nbr;        // [cap][n] list entries (ent_make)
   int* ncnt;       // [n]
+  // pair halving (mixed precision; null: off): per 32-slot tile the pairs it
+  // evaluates, and for each list entry where its force is found
+  int* evl;        // [nseg][EVL_CAP] partner slot | owner lane << 26
+  uint2* psrc;     // [n] byte q (q < 8): the evaluated pair holding list entry q's force; bit 7: negated
+  int* tcnt;       // [nseg] evaluated pairs of the tile, or -1: the tile evaluates its list as it stands
   // circular molecules: junction owners (8 per ring)
   int64_t n_junc;
   const int64_t* jslot;  // [n_junc] slot of each junction owner
@@ -142,7 +149,7 @@ struct KArgs {
   float Lf[3];
   float invLf[3];
   double L[3];
-  double fixS[3];   // fixed-point mirror: grid units per nm (2^32 / L periodic, 2^29 open)
+  double fixS[3];   // fixed-point mirror: grid units per nm (2^32 m / L periodic, 2^29 open)
   float fixSf[3];   // the same in FP32
   float fixq[3];    // nm per grid unit
   // molecules

@@ -24,7 +24,7 @@ struct SegSmem {
   Real* cn;          // [6][RING] ... on the owner's next nucleotide
   Real* cp;          // [3][RING] ... on the owner's previous patch (bending)
   int* pst;          // [SEG] first pair index of each nucleotide of the tile (warp_pairs)
-  Real* pf;          // [2 SEG][3] pair forces of one round of warp_pairs
+  Real* pf;          // [EVL_CAP][3] pair forces of a round of warp_pairs (64), or of a halved tile
 };
 
 template <class Real>
@@ -32,7 +32,7 @@ __host__ __device__ constexpr size_t seg_warp_bytes() {
   size_t b = sizeof(SPos<Real>) * RING + sizeof(int) * RING;
   b = (b + 15) & ~(size_t)15;
   b += sizeof(Real) * (size_t)RING * 15;
-  b += sizeof(int) * 32 + sizeof(Real) * 2 * 32 * 3;
+  b += sizeof(int) * 32 + sizeof(Real) * EVL_CAP * 3;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -53,7 +53,7 @@ __device__ __forceinline__ SegSmem<Real> carve(unsigned char* raw, int /*T*/) {
   s.cn = s.cs + (size_t)RING * 6;
   s.cp = s.cn + (size_t)RING * 6;
   s.pf = s.cp + (size_t)RING * 3;
-  s.pst = reinterpret_cast<int*>(s.pf + 2 * 32 * 3);
+  s.pst = reinterpret_cast<int*>(s.pf + EVL_CAP * 3);
   return s;
 }
 
@@ -377,7 +377,15 @@ __device__ __forceinline__ V3<Real> pair_force(const KArgs<Real>& a, int cur, un
       R.z += (double)(img_comp(img_me, 2) - img_comp(wj, 2) + ent_shift(ent, 2)) * a.L[2];
     }
   }
-  const V3<Real> d = R - h * uj + h * um;   // bead_j - bead_me
+  // bead_j - bead_me; in FP32 formed as fma(h, u_me - u_j, R), which is
+  // antisymmetric bit for bit (the pair force from the partner's side is
+  // exactly its negative), as pair halving needs
+  V3<Real> d;
+  if constexpr (sizeof(Real) == 4) {
+    d = V3<Real>{fmaf(h, um.x - uj.x, R.x), fmaf(h, um.y - uj.y, R.y), fmaf(h, um.z - uj.z, R.z)};
+  } else {
+    d = R - h * uj + h * um;
+  }
   const bool cross_strand = ((gu ^ (unsigned)j) & 1u) != 0;
   // typed sigma (Sec. 2, reading A1): two steric beads (either strand) at
   // sigma_ss, or at sigma_cross_steric across strands when that is set; any
@@ -411,6 +419,42 @@ __device__ __forceinline__ void warp_pairs(const KArgs<Real>& a, const SegSmem<R
   const int lane = threadIdx.x & 31;
   const int64_t B = g - lane;
   const unsigned ns = (unsigned)a.ns;
+  if constexpr (sizeof(Real) == 4) {
+    // pair halving: the tile's pairs evaluated once each (k_rebuild_pack),
+    // 32 at a time, then every nucleotide adds its list entries' forces in
+    // list order, negating those its partner evaluated
+    const int tc = a.evl ? a.tcnt[(unsigned)(B >> 5)] : -1;
+    if (tc >= 0) {
+      // the list count and entry codes first, so that their latency overlaps the evaluation
+      const int nn = act ? a.ncnt[(unsigned)g] : 0;
+      const uint2 cw = act ? a.psrc[(unsigned)g] : make_uint2(0u, 0u);
+      const int* ev = a.evl + (size_t)(B >> 5) * EVL_CAP;
+#pragma unroll
+      for (int k = 0; k < EVL_CAP / SEG; ++k) {
+        const int p = k * SEG + lane;
+        if (p < tc) {
+          const int e = ev[p];
+          const int L = (e >> 26) & 31;
+          const int rL = ring(B + L);
+          const SPos<Real>& mL = sm.pos[rL];
+          const V3<Real> fw = pair_force(a, cur, (unsigned)(B + L), mL, uvec(mL), sm.flg[rL], 0, e & ENT_JMASK,
+                                         (V3<Real>*)nullptr, (Real*)nullptr);
+          Real* o = sm.pf + 3 * p;
+          o[0] = fw.x; o[1] = fw.y; o[2] = fw.z;
+        }
+      }
+      __syncwarp();
+      for (int q = 0; q < nn; ++q) {
+        const unsigned c = ((q < 4 ? cw.x : cw.y) >> (8 * (q & 3))) & 255u;
+        const Real* o = sm.pf + 3 * (c & 127u);
+        const unsigned sg = (c & 128u) << 24;   // sign bit of a negated force
+        Fb += V3<Real>{__uint_as_float(__float_as_uint(o[0]) ^ sg), __uint_as_float(__float_as_uint(o[1]) ^ sg),
+                       __uint_as_float(__float_as_uint(o[2]) ^ sg)};
+      }
+      __syncwarp();
+      return;
+    }
+  }
   const int nn = act ? a.ncnt[(unsigned)g] : 0;
   int incl = nn;
 #pragma unroll

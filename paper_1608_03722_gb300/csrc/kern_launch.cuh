@@ -94,6 +94,13 @@ cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st)
                                                                   (int64_t)nsm * std::max(1, lbps)));
     k_rebuild_list<Real, CAPMAX><<<lgrid, LT, 0, st>>>(a);
   }
+  if (a.evl) {   // pair halving: the tiles' evaluated pairs, one resident wave of warps
+    int pbps = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pbps, k_rebuild_pack<Real>, PACK_WARPS * 32, 0);
+    const int pgrid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((a.nseg + PACK_WARPS - 1) / PACK_WARPS, (int64_t)nsm * std::max(1, pbps)));
+    k_rebuild_pack<Real><<<pgrid, PACK_WARPS * 32, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

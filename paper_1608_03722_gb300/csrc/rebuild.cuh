@@ -754,6 +754,102 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list(const KArgs<Re
   }
 }
 
+// R5 (mixed precision, pair halving): Newton's third law within a tile.  A
+// list pair whose nucleotides lie in the same 32-slot tile of the step
+// kernel is evaluated once, by its lower slot, and the other nucleotide
+// takes its force negated; a pair across tiles is evaluated by both of its
+// nucleotides, each for itself.  Per tile (one warp, one lane per slot): the
+// evaluated pairs in order (partner slot | owner lane << 26, lane by lane in
+// list order) and, for every list entry, the index of the evaluated pair
+// that holds its force (bit 7: negated), eight one-byte codes per slot.  An
+// entry is a mirror only when the partner's list holds the pair too (a list
+// built from the two sides can disagree at the list radius).  A tile with a
+// list longer than HALF_NMAX or more than EVL_CAP evaluated pairs is marked
+// -1 and evaluates its list as it stands.  The pair force is antisymmetric
+// bit for bit, so both ways give the same force sums.
+// Lists are sorted by partner slot, so a list holds its partners below the
+// tile, then its partners in the tile (ascending lane), then those above;
+// with the in-tile partners as a lane bitmask the position of any in-tile
+// pair in either list is a population count.
+constexpr int PACK_WARPS = 8;
+template <class Real>
+__global__ void __launch_bounds__(PACK_WARPS * 32) k_rebuild_pack(const KArgs<Real> a) {
+  __shared__ unsigned s_tm[PACK_WARPS][32];   // in-tile partners of each lane (bit = lane)
+  __shared__ int s_base[PACK_WARPS][32];      // first evaluated-pair index + partners below the tile - mirrors
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned ns = (unsigned)a.ns;
+  const unsigned below = (1u << lane) - 1u;
+  for (int64_t t = (int64_t)blockIdx.x * PACK_WARPS + w; t < a.nseg; t += (int64_t)gridDim.x * PACK_WARPS) {
+    const int64_t g = t * 32 + lane;
+    const bool in = g < a.n;
+    const int nn = in ? a.ncnt[g] : 0;
+    int e8[HALF_NMAX];   // the entries, all loads in flight at once
+#pragma unroll
+    for (int q = 0; q < HALF_NMAX; ++q) e8[q] = q < nn ? a.nbr[(unsigned)q * ns + (unsigned)g] : 0;
+    if (__any_sync(0xffffffffu, nn > HALF_NMAX)) {
+      if (lane == 0) a.tcnt[t] = -1;
+      continue;
+    }
+    const int t0 = (int)(t * 32);
+    int lo = 0;        // partners below the tile
+    unsigned tm = 0;   // partners in the tile
+#pragma unroll
+    for (int q = 0; q < HALF_NMAX; ++q) {
+      const int j = e8[q] & ENT_JMASK;
+      if (q < nn) {
+        if (j < t0) ++lo;
+        else if (j < t0 + 32) tm |= 1u << (j - t0);
+      }
+    }
+    s_tm[w][lane] = tm;
+    __syncwarp();
+    // mirrors: in-tile partners below this lane whose list holds this lane too
+    unsigned mm = 0;
+    for (unsigned c = tm & below; c; c &= c - 1u) {
+      const int k = __ffs(c) - 1;
+      if ((s_tm[w][k] >> lane) & 1u) mm |= 1u << k;
+    }
+    const int ne = nn - __popc(mm);
+    int incl = ne;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - ne;
+    if (total > EVL_CAP) {
+      if (lane == 0) a.tcnt[t] = -1;
+      __syncwarp();
+      continue;
+    }
+    // the pair (this lane, partner lane l > this lane) sits at list position
+    // lo + popc(tm below l), after every mirror of this lane
+    s_base[w][lane] = excl + lo - __popc(mm);
+    __syncwarp();
+    unsigned code[2] = {0u, 0u};
+    int r = 0;
+#pragma unroll
+    for (int q = 0; q < HALF_NMAX; ++q) {
+      if (q < nn) {
+        const int j = e8[q] & ENT_JMASK;
+        const int k = j - t0;
+        unsigned c;
+        if (k >= 0 && k < 32 && ((mm >> k) & 1u)) {   // the partner evaluates it: negated
+          c = 0x80u | (unsigned)(s_base[w][k] + __popc(s_tm[w][k] & below));
+        } else {
+          a.evl[t * EVL_CAP + excl + r] = j | (lane << 26);
+          c = (unsigned)(excl + r);
+          ++r;
+        }
+        code[q >> 2] |= c << (8 * (q & 3));
+      }
+    }
+    if (in) a.psrc[g] = make_uint2(code[0], code[1]);
+    if (lane == 0) a.tcnt[t] = total;
+    __syncwarp();
+  }
+}
+
 template <class Real>
 __global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list_lanes_hash(const KArgs<Real> a) {
   __shared__ int sent[LIST_WARPS][32][LIST_CAP];
