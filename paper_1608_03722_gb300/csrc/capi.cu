@@ -321,7 +321,7 @@ static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
   a.nsteps = 0; a.noise_mode = c->p.noise;
   a.bubble = c->p.bubble_rule;
   a.n_junc = c->n_junc; a.jslot = c->jslot; a.jidx = c->jidx; a.jout = (Real*)c->jout;
-  a.seed_lo = (uint32_t)c->p.seed; a.seed_hi = (uint32_t)(c->p.seed >> 32);
+  philox_key_schedule(a, c->p.seed);
   a.spin_budget = 4000000000ull;
   a.X = c->X; a.V = c->V; a.Om = (Real*)c->Om; a.Kw = c->Kw; a.U = c->U; a.ud = c->ud;
   a.topo = c->topo; a.img = c->img; a.kref = c->kref; a.nbr = c->nbr; a.ncnt = c->ncnt;

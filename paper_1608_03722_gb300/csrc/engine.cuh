@@ -107,7 +107,7 @@ struct KArgs {
   int cap;
   int64_t nsteps;
   int noise_mode;
-  uint32_t seed_lo, seed_hi;
+  uint32_t pkey[20];   // Philox round keys: (seed_lo + r W0, seed_hi + r W1) for rounds r = 0 .. 9
   unsigned long long spin_budget;
   // state
   // [k][n] below means k rows of ns entries (slots n .. ns-1 are padding)
@@ -170,6 +170,18 @@ struct KArgs {
   cudaGraphConditionalHandle h_while;
 };
 
+// Philox4x32-10 round keys of a 64-bit seed (Weyl sequence of the key).
+template <class Real>
+inline void philox_key_schedule(KArgs<Real>& a, uint64_t seed) {
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    a.pkey[2 * r] = k0;
+    a.pkey[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
 // Mirror grid of axis k (a.periodic and a.L set): 2^32 units per L / m with
 // m = max(1, floor(L / 8 nm)) in a periodic box, so that 32-bit wrap-around
 // differences are minimum-image separations, or 2^29 units per nm in an
@@ -216,16 +228,17 @@ __device__ __forceinline__ void sincos_(double a, double* s, double* c) { sincos
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Counter-based generator of Salmon et al. (SC'11): ten rounds, multipliers
-// 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.
-__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+// 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.  The
+// key schedule is the same for every counter, so the host computes it once
+// (philox_key_schedule) and each round reads its key pair from the kernel
+// parameters.
+__device__ __forceinline__ uint4 philox10(uint4 c, const uint32_t* key) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t a = c.x, b = c.z;
     const uint32_t hi_a = __umulhi(0xD2511F53u, a), lo_a = 0xD2511F53u * a;
     const uint32_t hi_b = __umulhi(0xCD9E8D57u, b), lo_b = 0xCD9E8D57u * b;
-    c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
+    c = make_uint4(hi_b ^ c.y ^ key[2 * r], lo_b, hi_a ^ c.w ^ key[2 * r + 1], lo_a);
   }
   return c;
 }
@@ -246,8 +259,7 @@ __device__ __forceinline__ void nucleotide_noise(const KArgs<Real>& a, uint32_t 
     ep = eb;
     return;
   }
-  const uint4 r = philox10(make_uint4(local, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)mol),
-                           a.seed_lo, a.seed_hi);
+  const uint4 r = philox10(make_uint4(local, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)mol), a.pkey);
   const uint32_t k[6] = {r.x >> 11, r.y >> 11, r.z >> 11, r.w >> 11, (r.x & 0x7FFu) | ((r.y & 0x3FFu) << 11),
                          (r.z & 0x7FFu) | ((r.w & 0x3FFu) << 11)};
   Real e[6];

@@ -665,9 +665,8 @@ __device__ __forceinline__ void nucleotide_pass(const KArgs<Real>& a, const SegS
             un = cs * um + sn * cross(ax, um);
             un = rsqrt_(dot(un, un)) * un;
           }
-          if (!(isfinite(Ft.x) && isfinite(Ft.y) && isfinite(Ft.z) && isfinite(Om.x) && isfinite(Om.y) &&
-                isfinite(Om.z)))
-            fl |= B_ENAN;
+          // a NaN or infinity in any component makes the sum non-finite
+          if (!isfinite((Ft.x + Ft.y) + (Ft.z + Om.x) + (Om.y + Om.z))) fl |= B_ENAN;
           a.V[gu] = Vd[0]; a.V[ns + gu] = Vd[1]; a.V[2 * ns + gu] = Vd[2];
           a.Om[gu] = Om.x; a.Om[ns + gu] = Om.y; a.Om[2 * ns + gu] = Om.z;
           if constexpr (sizeof(Real) == 4) {

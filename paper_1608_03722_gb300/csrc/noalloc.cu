@@ -213,7 +213,8 @@ extern "C" int dsdna_forces_noalloc(const dsdna_params* p, int n_mol, const int*
   KArgs<float> a{};
   fill_coef_mixed(q, a.c);   // list radius from the same skin as the cell edge
   a.n = n; a.ns = NA_MAX_NT; a.n_mol = n_mol; a.nseg = (n + 31) / 32; a.cap = NA_CAP;
-  a.nsteps = 0; a.noise_mode = 0; a.seed_lo = 0; a.seed_hi = 0;
+  a.nsteps = 0; a.noise_mode = 0;
+  philox_key_schedule(a, 0);
   a.bubble = p->bubble_rule ? 1 : 0;   // one evaluation without history: rule 2 removes what rule 1 does
   const bool ext = a.bubble != 0;
   a.n_junc = 0; a.jslot = nullptr; a.jidx = nullptr; a.jout = nullptr;   // linear molecules only
