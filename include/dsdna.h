@@ -353,8 +353,9 @@ int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys, const dsdn
  * Scratch memory: one fixed device array of about 5 MB (cell table,
  * neighbour list, position mirrors), reserved on every GPU that loads the
  * library until the process exits.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current; make
- * that first call before any stream capture.  Every call reuses the same
+ * array's device address (cudaGetSymbolAddress) with the device current.  No
+ * call can be captured into a CUDA graph: each copies the molecule table
+ * from host memory and waits for its stream.  Every call reuses the same
  * array and starts by clearing what must begin at zero; calls that overlap on
  * the GPU (other streams, other host threads) race on it and must be
  * serialised by the caller.  Returns DSDNA_OK or a negative dsdna_status
