@@ -430,6 +430,8 @@ def main():
     ap.add_argument("--skin", type=float, default=None, help="fixed skin (skips the autotuner)")
     ap.add_argument("--block-threads", type=int, default=None, help="fixed CTA size (skips the autotuner)")
     ap.add_argument("--no-compare", action="store_true", help="skip the batched / FP64 per-molecule comparison")
+    ap.add_argument("--list-build", type=int, default=0, choices=[0, 1],
+                    help="periodic neighbour-list build: 0 chain window, 1 cell walk")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     ws, rank, local = dist_env()
@@ -448,7 +450,7 @@ def main():
 
     cfg, desc = build_workload(args.workload, seed=rank, n_bp=args.n_bp)
     prec = D.PREC_MIXED if args.precision == "mixed" else D.PREC_FP64
-    p = D.dsdna_default_params(precision=prec, box=cfg.box, seed=rank)
+    p = D.dsdna_default_params(precision=prec, box=cfg.box, seed=rank, list_build=args.list_build)
     tuned = None
     if args.skin is not None or args.block_threads is not None:
         args.no_autotune = True
@@ -499,9 +501,11 @@ def main():
     rebuilds = info1["rebuilds"] - info0["rebuilds"]
     engine_launches = info1["engine_launches"] - info0["engine_launches"]
     # kernels of the timed region: per graph launch one loop-init kernel; per loop
-    # iteration one loop-head kernel and one persistent step kernel; five per rebuild
-    # unless the step kernel rebuilds the list itself
-    gpu_launches = graph_launches + 2 * engine_launches + (0 if info1["rebuild_in_step"] else 5 * rebuilds)
+    # iteration one loop-head kernel and one persistent step kernel; per rebuild five
+    # (chain-window build, or a cell walk without pair halving) or six (a cell walk
+    # and its pair-halving pack), none when the step kernel rebuilds the list itself
+    per_rebuild = 5 if (info1["chain_list"] or info1["halved_tiles"] == 0) else 6
+    gpu_launches = graph_launches + 2 * engine_launches + (0 if info1["rebuild_in_step"] else per_rebuild * rebuilds)
 
     # Roofline of the dominant kernel: K x S further steps queued launch by launch
     # (dsdna_step_profiled), each step-kernel launch bracketed by CUDA events on
@@ -612,6 +616,7 @@ def main():
             "config": {"workload": desc, "md_steps_per_step": S, "n_nucleotides": cfg.n_nt,
                        "parallelism": f"replicas x{ws}", "l2": "inputs larger than L2 (state > 129 MB)",
                        "rebuilds_in_timed_region": rebuilds, "graph_steps_per_launch": graph_chunk,
+                       "list_build": "chain window" if info1["chain_list"] else "cell walk",
                        "autotuned": tuned},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "compare": compare,
             "gpu_launches": gpu_launches, "clocks": clocks,

@@ -103,6 +103,9 @@ enum { DSDNA_NOISE_OFF = 0, DSDNA_NOISE_UNIFORM = 1, DSDNA_NOISE_GAUSSIAN = 2 };
  * gamma = 1, dt = 0.005 tau_Br, Eq. 16). */
 /* rebuild_mode 0 rebuilds inside the step kernel up to this many nucleotides */
 #define DSDNA_FUSED_REBUILD_MAX_NT 262144
+/* Chain-window list build: radius (nm) of the widest 16-slot segment (8 base
+ * pairs; about 1.3 nm in the relaxed helix) that enters the segment grid whole. */
+#define DSDNA_SEG_RCAP 1.8
 
 typedef struct dsdna_params {
   double K1, R0, eps_bb, sigma_bb;       /* FENE + backbone WCA */
@@ -158,6 +161,18 @@ typedef struct dsdna_params {
    * list pair from both sides.  The pair force is antisymmetric bit for bit,
    * so both give the same forces and trajectories bit for bit. */
   int pair_halving;
+  /* Neighbour-list build in the separate rebuild kernels and the force and
+   * energy passes (the rebuild inside the step kernel, rebuild_mode 2, walks
+   * cells).  0: chain-window build: every pair of beads whose 16-slot
+   * segments (8 base pairs) are equal or adjacent is tested directly from
+   * shared memory, and the other pairs are found through a grid of segment
+   * bounding spheres (Sec. 6 lists, arranged for a chain whose list partners
+   * are nearly all a few slots away); a periodic box uses it when that grid
+   * has at least 3 cells per edge and its cell table is linear, an open box
+   * always.  1: the cell walk (one lane per bead over its 27 neighbour
+   * cells).  Both give the same pairs (up to pairs within FP32 rounding of
+   * the list radius, which lie beyond every cutoff) in the same order. */
+  int list_build;
 } dsdna_params;
 
 /* Molecules and (optional) initial state.  NULL X/u builds ideal relaxed
@@ -217,6 +232,7 @@ typedef struct dsdna_info {
   int rebuild_in_step;   /* 1: the step kernel rebuilds the list itself (rebuild_mode) */
   int64_t halved_tiles;  /* 32-slot tiles whose same-tile list pairs the last build set to be evaluated
                             once (pair_halving); 0 when pair halving is off */
+  int chain_list;        /* 1: the chain-window list build runs (list_build) */
 } dsdna_info;
 
 /* Per-launch timing of dsdna_step_profiled (CUDA events on the context stream). */

@@ -22,6 +22,7 @@ namespace dsdna {
 template <class Real> cudaError_t engine_occupancy(int mode, int T, int* blocks_per_sm, size_t* smem);
 template <class Real> cudaError_t engine_launch(int mode, const KArgs<Real>& a, int grid, int T, size_t smem, cudaStream_t st);
 template <class Real> cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st);
+template <class Real> cudaError_t rebuild_prepare();
 }  // namespace dsdna
 
 using namespace dsdna;
@@ -76,6 +77,15 @@ struct dsdna_ctx {
   int morton_bits = 0;
   int nc[3] = {0, 0, 0};
   double cellh = 0;
+  // chain-window list build (periodic box with a linear table, or open box):
+  // the separate rebuild kernels and the force and energy passes; the
+  // in-kernel rebuild keeps the cell walk
+  bool chain = false;
+  float4* segc = nullptr;
+  int sg_nc[3] = {0, 0, 0};
+  double sg_edge = 0;
+  unsigned sg_H = 0, sg_mask = 0;
+  unsigned H_alloc = 0;          // entries of cnt (start: one more), for either table
   // launch
   int T = 256;
   int64_t nseg = 0;
@@ -328,6 +338,16 @@ static void fill_args(dsdna_ctx* c, KArgs<Real>& a) {
   a.evl = sizeof(Real) == 4 ? c->evl : nullptr; a.psrc = c->psrc; a.tcnt = c->tcnt;
   a.cnt = c->cnt; a.start = c->start; a.H = c->H; a.table = c->table; a.morton_bits = c->morton_bits; a.key = c->key;
   a.cent = c->cent; a.wpos = c->wpos; a.bsum = c->bsum;
+  a.segc = c->chain ? c->segc : nullptr;
+  a.nseg16 = (c->n + 15) / 16;
+  a.sg_H = c->sg_H;
+  a.sg_mask = c->sg_mask;
+  a.sg_rcap = (float)DSDNA_SEG_RCAP;
+  a.sg_reach = std::sqrt(a.c.rl_max2) + 0.002f;   // margin over the FP32 rounding of centres and radii
+  for (int k = 0; k < 3; ++k) {
+    a.sg_nc[k] = c->sg_nc[k];
+    a.sg_invh[k] = !c->chain ? 0.0f : (float)(c->p.box[0] > 0.0 ? c->sg_nc[k] / c->p.box[k] : 1.0 / c->sg_edge);
+  }
   a.periodic = c->p.box[0] > 0.0 ? 1 : 0;
   for (int k = 0; k < 3; ++k) {
     a.nc[k] = c->nc[k];
@@ -362,6 +382,7 @@ static int validate(const dsdna_params* p, const dsdna_system* s) {
   if (p->bubble_rule < 0 || p->bubble_rule > 2) return fail(nullptr, DSDNA_EINVAL, "bubble_rule must be 0, 1 or 2");
   if (p->rebuild_mode < 0 || p->rebuild_mode > 2) return fail(nullptr, DSDNA_EINVAL, "rebuild_mode must be 0, 1 or 2");
   if (p->pair_halving < 0 || p->pair_halving > 1) return fail(nullptr, DSDNA_EINVAL, "pair_halving must be 0 or 1");
+  if (p->list_build < 0 || p->list_build > 1) return fail(nullptr, DSDNA_EINVAL, "list_build must be 0 or 1");
   if (p->K2_gc < 0.0) return fail(nullptr, DSDNA_EINVAL, "K2_gc must be >= 0");
   if (p->noise < 0 || p->noise > 2) return fail(nullptr, DSDNA_EINVAL, "noise mode");
   if (p->steric_phase < 0 || p->steric_phase > 2) return fail(nullptr, DSDNA_EINVAL, "steric_phase must be 0, 1 or 2");
@@ -493,6 +514,31 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
   // rebuild inside the step kernel: small systems, linear or hashed table
   c->fused = c->table != TABLE_MORTON &&
              (c->p.rebuild_mode == 2 || (c->p.rebuild_mode == 0 && n <= DSDNA_FUSED_REBUILD_MAX_NT));
+  // chain-window list build: a grid of 16-slot segments whose cells span two
+  // of the widest segments kept whole plus the list radius; in a periodic box
+  // at least 3 cells per edge, in an open box hashed (at most half full with
+  // whole segments)
+  c->sg_edge = (2.0 * DSDNA_SEG_RCAP + rmax) * 1.001 + 0.01;
+  if (c->table == TABLE_LINEAR && c->p.list_build == 0) {
+    bool fits = true;
+    uint64_t cells = 1;
+    for (int k = 0; k < 3; ++k) {
+      c->sg_nc[k] = (int)std::floor(c->p.box[k] / c->sg_edge);
+      fits = fits && c->sg_nc[k] >= 3;
+      cells *= (uint64_t)std::max(1, c->sg_nc[k]);
+    }
+    if (fits) {
+      c->chain = true;
+      c->sg_H = (unsigned)((cells + 1 + 2047) / 2048 * 2048);   // start[cells] is a scanned entry
+    }
+  } else if (c->table == TABLE_HASH && c->p.list_build == 0) {
+    unsigned Hs = 2048;
+    while ((int64_t)Hs < n / 8) Hs <<= 1;
+    c->chain = true;
+    c->sg_mask = Hs - 1;
+    c->sg_H = Hs + 2048;   // a last tile of empty entries: start[Hs] is a scanned entry
+  }
+  c->H_alloc = std::max(c->H, c->sg_H);
 
   // allocations
   const bool f64 = c->fp64();
@@ -522,8 +568,9 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
     const size_t nt = (nn + SEG_SLOTS - 1) / SEG_SLOTS;
     ALLOC(evl, int, nt * EVL_CAP); ALLOC(psrc, uint2, ns); ALLOC(tcnt, int, nt);
   }
-  ALLOC(cnt, unsigned, c->H); ALLOC(start, unsigned, (size_t)c->H + 1); ALLOC(key, int, nn);
+  ALLOC(cnt, unsigned, c->H_alloc); ALLOC(start, unsigned, (size_t)c->H_alloc + 1); ALLOC(key, int, nn);
   ALLOC(cent, float4, nn); ALLOC(wpos, float4, nn);
+  if (c->chain) ALLOC(segc, float4, (nn + 15) / 16 + 1);
   ALLOC(mol_off, int64_t, c->n_mol + 1); ALLOC(ext_d, double, (size_t)c->n_mol * 8);
   ALLOC(bar, GridBar, 1); ALLOC(err, unsigned, 4); ALLOC(step_d, int64_t, 1); ALLOC(rebuild, int, 4);
   ALLOC(nrebuild, unsigned long long, 1);
@@ -546,6 +593,10 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
     if (e != cudaSuccess || bps < 1) return bad(fail(c, DSDNA_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e)));
     if (c->p.blocks_per_sm > 0) bps = std::min(bps, c->p.blocks_per_sm);
     c->grid[mode] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * nsm, c->nseg));
+  }
+  if (c->chain) {
+    const cudaError_t e = f64 ? rebuild_prepare<double>() : rebuild_prepare<float>();
+    if (e != cudaSuccess) return bad(fail(c, DSDNA_ECUDA, std::string("rebuild kernel attributes: ") + cudaGetErrorString(e)));
   }
   c->scan_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 8, ((int64_t)c->H + 2047) / 2048));
   // block sums: one per CTA of the scan kernels, or of the step kernel when it rebuilds
@@ -603,7 +654,7 @@ extern "C" int dsdna_create(const dsdna_params* params, const dsdna_system* sys,
       cpy(c->mol_off, c->off.data(), sizeof(int64_t) * (c->n_mol + 1)) != cudaSuccess ||
       cpy(c->ext_d, c->ext.data(), sizeof(double) * c->ext.size()) != cudaSuccess)
     return bad(fail(c, DSDNA_ECUDA, "topology upload"));
-  if (cudaMemset(c->cnt, 0, sizeof(unsigned) * c->H) != cudaSuccess || cudaMemset(c->err, 0, 16) != cudaSuccess ||
+  if (cudaMemset(c->cnt, 0, sizeof(unsigned) * c->H_alloc) != cudaSuccess || cudaMemset(c->err, 0, 16) != cudaSuccess ||
       cudaMemset(c->step_d, 0, 8) != cudaSuccess || cudaMemset(c->nrebuild, 0, 8) != cudaSuccess ||
       cudaMemset(c->nlaunch, 0, 8) != cudaSuccess ||
       cudaMemset(c->bar, 0, sizeof(GridBar)) != cudaSuccess || cudaMemset(c->ncnt, 0, sizeof(int) * ns) != cudaSuccess ||
@@ -1118,6 +1169,7 @@ extern "C" int dsdna_get_info(const dsdna_ctx* c, dsdna_info* info) {
   cudaMemcpy(&nb, c->nlaunch, sizeof(nb), cudaMemcpyDeviceToHost);
   info->engine_launches = (int64_t)nb + c->host_launches;
   info->rebuild_in_step = c->fused ? 1 : 0;
+  info->chain_list = c->chain ? 1 : 0;
   info->grid_blocks = c->grid[MODE_STEP];
   info->block_threads = c->T;
   info->max_neighbors = c->p.max_neighbors;

@@ -142,6 +142,18 @@ struct KArgs {
   float4* cent;    // [n] cell-sorted (position, slot)
   float4* wpos;    // [n] wrapped bead position, w = molecule
   unsigned* bsum;  // [grid]
+  // chain-window list build (null segc: the cell-walk build).  The cell
+  // table above then holds a grid of 16-slot segments (linear in a periodic
+  // box, hashed in an open one), cent their bounding spheres and key their
+  // slot ranges.
+  float4* segc;      // [nseg16] each segment's bounding sphere: wrapped centre, radius (< 0: wide)
+  int64_t nseg16;
+  int sg_nc[3];      // cells per edge of the segment grid
+  float sg_invh[3];  // cells per nm
+  unsigned sg_H;     // entries of the segment table scan (whole scan tiles, more than its cells)
+  unsigned sg_mask;  // open box: the table is hashed into sg_mask + 1 entries
+  float sg_rcap;     // widest segment kept whole in the grid
+  float sg_reach;    // largest list radius plus a margin (sphere test)
   int periodic;
   int nc[3];
   float cellh[3];

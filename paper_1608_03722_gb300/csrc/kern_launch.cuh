@@ -5,6 +5,7 @@
 
 #include "engine_kernels.cuh"
 #include "rebuild.cuh"
+#include "chainlist.cuh"
 
 namespace dsdna {
 
@@ -61,7 +62,18 @@ cudaError_t engine_launch(int mode, const KArgs<Real>& a, int grid, int T, size_
   return cudaLaunchKernelExC(&cfg, engine_fn<Real>(mode), args);
 }
 
-// The five rebuild kernels on stream st (grid-stride; the scan pair shares one grid).
+// Kernel attributes of the rebuild kernels for the current device, set when a
+// context is created: the chain-window list build asks for the largest
+// shared-memory carveout, so that four of its CTAs (47 KB of shared memory
+// each) are resident per SM.
+template <class Real>
+cudaError_t rebuild_prepare() {
+  return cudaFuncSetAttribute(k_rebuild_list_chain<Real>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
+// The rebuild kernels on stream st (grid-stride; the scan pair shares one grid):
+// five for the chain-window build, five or six (pair halving) for the cell walks.
 template <class Real>
 cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st) {
   const int T = 256;
@@ -70,6 +82,24 @@ cudaError_t rebuild_launch(const KArgs<Real>& a, int scan_grid, cudaStream_t st)
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (a.n + T - 1) / T;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 16));
+  if (a.segc) {
+    // chain-window build (periodic box): segment grid (bin, scan, scatter),
+    // then one warp per 32-slot tile builds its lists and their pair halving
+    KArgs<Real> as = a;
+    as.H = a.sg_H;
+    const int sgrid = std::max(1, std::min(scan_grid, (int)((a.sg_H + 2047u) / 2048u)));
+    k_rebuild_segbin<Real><<<grid, T, 0, st>>>(a);
+    k_rebuild_scan_a<Real><<<sgrid, T, 0, st>>>(as);
+    k_rebuild_scan_b<Real><<<sgrid, T, 0, st>>>(as);
+    const int64_t swant = (a.nseg16 + T - 1) / T;
+    k_rebuild_segscatter<Real><<<(int)std::max<int64_t>(1, std::min<int64_t>(swant, (int64_t)nsm * 16)), T, 0, st>>>(a);
+    int cbps = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cbps, k_rebuild_list_chain<Real>, CL_WARPS * 32, 0);
+    const int cgrid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((a.nseg + CL_WARPS - 1) / CL_WARPS, (int64_t)nsm * std::max(1, cbps)));
+    k_rebuild_list_chain<Real><<<cgrid, CL_WARPS * 32, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   k_rebuild_bin<Real><<<grid, T, 0, st>>>(a);
   k_rebuild_scan_a<Real><<<scan_grid, T, 0, st>>>(a);
   k_rebuild_scan_b<Real><<<scan_grid, T, 0, st>>>(a);

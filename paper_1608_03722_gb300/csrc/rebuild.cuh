@@ -93,59 +93,68 @@ __device__ __forceinline__ void bead_position(const KArgs<Real>& a, int cur, int
   }
 }
 
+// Per-bead part of R1: the wrapped FP32 bead position (to wpos, with the
+// molecule), the periodic image word and the build-time mirror of the
+// rebuild trigger.  Returns the wrapped position in pw and the molecule.
+template <class Real>
+__device__ __forceinline__ int bin_bead(const KArgs<Real>& a, int cur, int64_t g, unsigned& fl, float* pw) {
+  // Binning in FP32: any integer image w with pw = b - w L is exact for the
+  // force path (it only uses integer image differences), so rounding here
+  // moves a bead by at most a few 1e-5 nm inside the 0.01 nm list margin.
+  float b[3];
+  bead_position_f(a, cur, g, b);
+  int w[3] = {0, 0, 0};
+  for (int c = 0; c < 3; ++c) {
+    float x = b[c];
+    if (a.periodic) {
+      const float q = floorf(x * a.invLf[c]);
+      w[c] = (int)q;
+      x = fmaf(-q, a.Lf[c], x);
+      if (w[c] > 511 || w[c] < -512) fl |= B_EIMG;
+    }
+    pw[c] = x;
+  }
+  // the image word (three signed 10-bit fields) also carries the bead's steric
+  // flag in bit 30, for the pair typing of the force loop
+  const int tp = a.topo[g];
+  const int packed = (w[0] & 0x3ff) | ((w[1] & 0x3ff) << 10) | ((w[2] & 0x3ff) << 20) | ((tp & F_STERIC) << IMG_STERIC_SHIFT);
+  const int mol = tp >> MOL_SHIFT;
+  a.wpos[g] = make_float4(pw[0], pw[1], pw[2], __int_as_float(mol));
+  if constexpr (sizeof(Real) == 8) a.img[g] = packed;   // mixed precision keeps it in Kw.w
+  // build-time bead position on the fixed-point grid, for the rebuild trigger
+  const float h = (float)a.c.h;
+  if constexpr (sizeof(Real) == 4) {
+    int4 kw = a.Kw[(size_t)cur * a.ns + g];
+    const float4 u = a.U[(size_t)cur * a.ns + g];
+    a.kref[g] = kw.x + bead_off(h * u.x, a.fixSf[0]);
+    a.kref[a.ns + g] = kw.y + bead_off(h * u.y, a.fixSf[1]);
+    a.kref[2 * a.ns + g] = kw.z + bead_off(h * u.z, a.fixSf[2]);
+    kw.w = packed;
+    a.Kw[(size_t)cur * a.ns + g] = kw;
+  } else {
+    const double* X = a.X + (size_t)cur * 3 * a.ns;
+    const double* u = a.ud + (size_t)cur * 3 * a.ns;
+    for (int c = 0; c < 3; ++c)
+      a.kref[c * a.ns + g] = fixs(X[c * a.ns + g], a.fixS[c]) + bead_off(h * (float)u[c * a.ns + g], a.fixSf[c]);
+  }
+  return mol;
+}
+
 // R1: bin beads, record images and the build-time mirror.
 template <class Real>
 __device__ void rebuild_bin(const KArgs<Real>& a, int cur, unsigned& fl) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.n; g += stride) {
-    // Binning in FP32: any integer image w with pw = b - w L is exact for the
-    // force path (it only uses integer image differences), so rounding here
-    // moves a bead by at most a few 1e-5 nm inside the 0.01 nm list margin.
-    float b[3];
-    bead_position_f(a, cur, g, b);
-    int w[3] = {0, 0, 0}, ci[3];
     float pw[3];
+    const int mol = bin_bead(a, cur, g, fl, pw);
+    int ci[3];
     for (int c = 0; c < 3; ++c) {
-      float x = b[c];
-      if (a.periodic) {
-        const float q = floorf(x * a.invLf[c]);
-        w[c] = (int)q;
-        x = fmaf(-q, a.Lf[c], x);
-        pw[c] = x;
-        int k = (int)floorf(x * a.invcellh[c]);
-        ci[c] = k >= a.nc[c] ? a.nc[c] - 1 : (k < 0 ? 0 : k);
-        if (w[c] > 511 || w[c] < -512) fl |= B_EIMG;
-      } else {
-        pw[c] = x;
-        ci[c] = (int)floorf(x * a.invcellh[c]);
-      }
+      const int k = (int)floorf(pw[c] * a.invcellh[c]);
+      ci[c] = a.periodic ? (k >= a.nc[c] ? a.nc[c] - 1 : (k < 0 ? 0 : k)) : k;
     }
-    // the image word (three signed 10-bit fields) also carries the bead's steric
-    // flag in bit 30, for the pair typing of the force loop
-    const int tp = a.topo[g];
-    const int packed = (w[0] & 0x3ff) | ((w[1] & 0x3ff) << 10) | ((w[2] & 0x3ff) << 20) | ((tp & F_STERIC) << IMG_STERIC_SHIFT);
-    const int mol = tp >> MOL_SHIFT;
     const unsigned k = cell_key(a, mol, ci[0], ci[1], ci[2]);
     a.key[g] = (int)k;
-    a.wpos[g] = make_float4(pw[0], pw[1], pw[2], __int_as_float(mol));
-    if constexpr (sizeof(Real) == 8) a.img[g] = packed;   // mixed precision keeps it in Kw.w
     atomicAdd(&a.cnt[k], 1u);
-    // build-time bead position on the fixed-point grid, for the rebuild trigger
-    const float h = (float)a.c.h;
-    if constexpr (sizeof(Real) == 4) {
-      int4 kw = a.Kw[(size_t)cur * a.ns + g];
-      const float4 u = a.U[(size_t)cur * a.ns + g];
-      a.kref[g] = kw.x + bead_off(h * u.x, a.fixSf[0]);
-      a.kref[a.ns + g] = kw.y + bead_off(h * u.y, a.fixSf[1]);
-      a.kref[2 * a.ns + g] = kw.z + bead_off(h * u.z, a.fixSf[2]);
-      kw.w = packed;
-      a.Kw[(size_t)cur * a.ns + g] = kw;
-    } else {
-      const double* X = a.X + (size_t)cur * 3 * a.ns;
-      const double* u = a.ud + (size_t)cur * 3 * a.ns;
-      for (int c = 0; c < 3; ++c)
-        a.kref[c * a.ns + g] = fixs(X[c * a.ns + g], a.fixS[c]) + bead_off(h * (float)u[c * a.ns + g], a.fixSf[c]);
-    }
   }
 }
 
@@ -772,81 +781,92 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_rebuild_list(const KArgs<Re
 // with the in-tile partners as a lane bitmask the position of any in-tile
 // pair in either list is a population count.
 constexpr int PACK_WARPS = 8;
+
+// Pair halving of tile t by one warp (lane = slot t * 32 + lane): nn list
+// entries of this lane, the first HALF_NMAX of them in e8; s_tm and s_base
+// are the warp's 32-entry shared scratch.  Every lane of the warp calls it.
+template <class Real>
+__device__ __forceinline__ void pack_tile(const KArgs<Real>& a, int64_t t, int lane, int nn, const int* e8,
+                                          unsigned* s_tm, int* s_base) {
+  const int64_t g = t * 32 + lane;
+  const bool in = g < a.n;
+  const unsigned below = (1u << lane) - 1u;
+  if (__any_sync(0xffffffffu, nn > HALF_NMAX)) {
+    if (lane == 0) a.tcnt[t] = -1;
+    return;
+  }
+  const int t0 = (int)(t * 32);
+  int lo = 0;        // partners below the tile
+  unsigned tm = 0;   // partners in the tile
+#pragma unroll
+  for (int q = 0; q < HALF_NMAX; ++q) {
+    const int j = e8[q] & ENT_JMASK;
+    if (q < nn) {
+      if (j < t0) ++lo;
+      else if (j < t0 + 32) tm |= 1u << (j - t0);
+    }
+  }
+  s_tm[lane] = tm;
+  __syncwarp();
+  // mirrors: in-tile partners below this lane whose list holds this lane too
+  unsigned mm = 0;
+  for (unsigned c = tm & below; c; c &= c - 1u) {
+    const int k = __ffs(c) - 1;
+    if ((s_tm[k] >> lane) & 1u) mm |= 1u << k;
+  }
+  const int ne = nn - __popc(mm);
+  int incl = ne;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - ne;
+  if (total > EVL_CAP) {
+    if (lane == 0) a.tcnt[t] = -1;
+    __syncwarp();
+    return;
+  }
+  // the pair (this lane, partner lane l > this lane) sits at list position
+  // lo + popc(tm below l), after every mirror of this lane
+  s_base[lane] = excl + lo - __popc(mm);
+  __syncwarp();
+  unsigned code[2] = {0u, 0u};
+  int r = 0;
+#pragma unroll
+  for (int q = 0; q < HALF_NMAX; ++q) {
+    if (q < nn) {
+      const int j = e8[q] & ENT_JMASK;
+      const int k = j - t0;
+      unsigned c;
+      if (k >= 0 && k < 32 && ((mm >> k) & 1u)) {   // the partner evaluates it: negated
+        c = 0x80u | (unsigned)(s_base[k] + __popc(s_tm[k] & below));
+      } else {
+        a.evl[t * EVL_CAP + excl + r] = j | (lane << 26);
+        c = (unsigned)(excl + r);
+        ++r;
+      }
+      code[q >> 2] |= c << (8 * (q & 3));
+    }
+  }
+  if (in) a.psrc[g] = make_uint2(code[0], code[1]);
+  if (lane == 0) a.tcnt[t] = total;
+  __syncwarp();
+}
+
 template <class Real>
 __global__ void __launch_bounds__(PACK_WARPS * 32) k_rebuild_pack(const KArgs<Real> a) {
   __shared__ unsigned s_tm[PACK_WARPS][32];   // in-tile partners of each lane (bit = lane)
   __shared__ int s_base[PACK_WARPS][32];      // first evaluated-pair index + partners below the tile - mirrors
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned ns = (unsigned)a.ns;
-  const unsigned below = (1u << lane) - 1u;
   for (int64_t t = (int64_t)blockIdx.x * PACK_WARPS + w; t < a.nseg; t += (int64_t)gridDim.x * PACK_WARPS) {
     const int64_t g = t * 32 + lane;
-    const bool in = g < a.n;
-    const int nn = in ? a.ncnt[g] : 0;
+    const int nn = g < a.n ? a.ncnt[g] : 0;
     int e8[HALF_NMAX];   // the entries, all loads in flight at once
 #pragma unroll
     for (int q = 0; q < HALF_NMAX; ++q) e8[q] = q < nn ? a.nbr[(unsigned)q * ns + (unsigned)g] : 0;
-    if (__any_sync(0xffffffffu, nn > HALF_NMAX)) {
-      if (lane == 0) a.tcnt[t] = -1;
-      continue;
-    }
-    const int t0 = (int)(t * 32);
-    int lo = 0;        // partners below the tile
-    unsigned tm = 0;   // partners in the tile
-#pragma unroll
-    for (int q = 0; q < HALF_NMAX; ++q) {
-      const int j = e8[q] & ENT_JMASK;
-      if (q < nn) {
-        if (j < t0) ++lo;
-        else if (j < t0 + 32) tm |= 1u << (j - t0);
-      }
-    }
-    s_tm[w][lane] = tm;
-    __syncwarp();
-    // mirrors: in-tile partners below this lane whose list holds this lane too
-    unsigned mm = 0;
-    for (unsigned c = tm & below; c; c &= c - 1u) {
-      const int k = __ffs(c) - 1;
-      if ((s_tm[w][k] >> lane) & 1u) mm |= 1u << k;
-    }
-    const int ne = nn - __popc(mm);
-    int incl = ne;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31), excl = incl - ne;
-    if (total > EVL_CAP) {
-      if (lane == 0) a.tcnt[t] = -1;
-      __syncwarp();
-      continue;
-    }
-    // the pair (this lane, partner lane l > this lane) sits at list position
-    // lo + popc(tm below l), after every mirror of this lane
-    s_base[w][lane] = excl + lo - __popc(mm);
-    __syncwarp();
-    unsigned code[2] = {0u, 0u};
-    int r = 0;
-#pragma unroll
-    for (int q = 0; q < HALF_NMAX; ++q) {
-      if (q < nn) {
-        const int j = e8[q] & ENT_JMASK;
-        const int k = j - t0;
-        unsigned c;
-        if (k >= 0 && k < 32 && ((mm >> k) & 1u)) {   // the partner evaluates it: negated
-          c = 0x80u | (unsigned)(s_base[w][k] + __popc(s_tm[w][k] & below));
-        } else {
-          a.evl[t * EVL_CAP + excl + r] = j | (lane << 26);
-          c = (unsigned)(excl + r);
-          ++r;
-        }
-        code[q >> 2] |= c << (8 * (q & 3));
-      }
-    }
-    if (in) a.psrc[g] = make_uint2(code[0], code[1]);
-    if (lane == 0) a.tcnt[t] = total;
-    __syncwarp();
+    pack_tile(a, t, lane, nn, e8, s_tm[w], s_base[w]);
   }
 }
 

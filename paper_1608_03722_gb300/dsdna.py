@@ -33,7 +33,8 @@ class dsdna_params(C.Structure):
         ("seed", C.c_uint64), ("noise", C.c_int), ("steric_phase", C.c_int), ("box", C.c_double * 3),
         ("skin", C.c_double), ("precision", C.c_int), ("max_neighbors", C.c_int), ("block_threads", C.c_int),
         ("blocks_per_sm", C.c_int), ("steps_per_graph", C.c_int), ("bubble_rule", C.c_int), ("K2_gc", C.c_double),
-        ("rebuild_mode", C.c_int), ("sigma_cross_steric", C.c_double), ("pair_halving", C.c_int)]
+        ("rebuild_mode", C.c_int), ("sigma_cross_steric", C.c_double), ("pair_halving", C.c_int),
+        ("list_build", C.c_int)]
 
 
 class dsdna_system(C.Structure):
@@ -78,7 +79,7 @@ class dsdna_info(C.Structure):
                 ("grid_blocks", C.c_int), ("block_threads", C.c_int), ("max_neighbors", C.c_int),
                 ("precision", C.c_int), ("skin", C.c_double), ("cell_table", C.c_int64),
                 ("device_bytes", C.c_int64), ("engine_launches", C.c_int64), ("rebuild_in_step", C.c_int),
-                ("halved_tiles", C.c_int64)]
+                ("halved_tiles", C.c_int64), ("chain_list", C.c_int)]
 
 
 class dsdna_prof(C.Structure):

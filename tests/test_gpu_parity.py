@@ -430,16 +430,21 @@ def test_profiles_sum_to_the_observables(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_open_box_list_with_shared_buckets_equals_brute_force(prec):
-    """Open box: the hashed table puts blocks of 8 x-cells in buckets; four
-    overlapping 400 bp molecules occupy about 500 blocks of 1024 buckets, so
-    two of the 9 rows of a bead share a bucket for a few percent of the 3200
-    beads.  The list holds each pair once and exactly the brute-force set."""
+@pytest.mark.parametrize("list_build", [0, 1])
+def test_open_box_list_with_shared_buckets_equals_brute_force(prec, list_build):
+    """Open box: the hashed table of the cell walk (list_build 1) puts blocks
+    of 8 x-cells in buckets; four overlapping 400 bp molecules occupy about
+    500 blocks of 1024 buckets, so two of the 9 rows of a bead share a bucket
+    for a few percent of the 3200 beads.  The chain-window build (list_build
+    0) hashes (molecule, cell) of its segments instead, and the overlapping
+    molecules share entries.  The list holds each pair once and exactly the
+    brute-force set."""
     rng = np.random.default_rng(3)
     parts = [I.wlc_helix(400, 50.0, rng) for _ in range(4)]
     X = np.concatenate([q[0] for q in parts]); u = np.concatenate([q[1] for q in parts])
     n_bp = [400] * 4
-    ctx = D.Context(D.dsdna_default_params(precision=prec), n_bp, X=X, u=u)
+    ctx = D.Context(D.dsdna_default_params(precision=prec, list_build=list_build), n_bp, X=X, u=u)
+    assert ctx.info()["chain_list"] == (list_build == 0)
     pl = ctx.neighbor_pairs()
     got = {tuple(x) for x in pl}
     assert len(pl) == len(got), "a pair listed twice"
@@ -452,7 +457,8 @@ def test_open_box_list_with_shared_buckets_equals_brute_force(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_open_box_list_across_hash_blocks_equals_brute_force(prec):
+@pytest.mark.parametrize("list_build", [0, 1])
+def test_open_box_list_across_hash_blocks_equals_brute_force(prec, list_build):
     """Open box, molecules spread over the hashed table's x-blocks of 8 cells:
     worm-like molecules with their origins at negative and positive x and y
     (some on block edges), one held along z through the origin (x-cells -1
@@ -470,7 +476,7 @@ def test_open_box_list_across_hash_blocks_equals_brute_force(prec):
     Xs.append(X @ R.T); us.append(u @ R.T)
     X = np.concatenate(Xs); u = np.concatenate(us)
     n_bp = [300] * 7
-    ctx = D.Context(D.dsdna_default_params(precision=prec), n_bp, X=X, u=u)
+    ctx = D.Context(D.dsdna_default_params(precision=prec, list_build=list_build), n_bp, X=X, u=u)
     pl = ctx.neighbor_pairs()
     got = {tuple(x) for x in pl}
     assert len(pl) == len(got), "a pair listed twice"
