@@ -335,7 +335,7 @@ void dsdna_destroy(dsdna_ctx* ctx);
  * the paper, which ran LAMMPS with hand-set neighbour settings, Sec. 6).
  * Runs trial_steps warm-up steps and trial_steps timed steps of the system
  * sys on temporary contexts for every candidate neighbour skin
- * (0.2 .. 0.6 nm), CTA size (128, 256, 1024) and persistent CTAs per SM (and, with
+ * (0.2, 0.25, 0.3, 0.35, 0.4, 0.5, 0.6 nm), CTA size (128, 256, 1024) and persistent CTAs per SM (and, with
  * rebuild_mode 0 and between a quarter and four times
  * DSDNA_FUSED_REBUILD_MAX_NT nucleotides, both rebuild paths), and writes
  * to *best the copy of *base with the fastest choice (ns per

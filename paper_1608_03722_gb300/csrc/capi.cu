@@ -1198,7 +1198,7 @@ extern "C" const char* dsdna_last_error(const dsdna_ctx* c) {
 extern "C" int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys, const dsdna_allocator* alloc,
                               void* cuda_stream, int trial_steps, dsdna_params* best, double* best_ns) {
   if (!base || !sys || !best || trial_steps < 1) return fail(nullptr, DSDNA_EINVAL, "autotune: bad arguments");
-  const double skins[] = {0.2, 0.3, 0.4, 0.5, 0.6};
+  const double skins[] = {0.2, 0.25, 0.3, 0.35, 0.4, 0.5, 0.6};
   const int blocks[] = {128, 256, 1024};
   const int per_sm[] = {0, 2};
   cudaStream_t st = (cudaStream_t)cuda_stream;
