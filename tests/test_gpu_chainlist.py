@@ -162,3 +162,59 @@ def test_chain_list_open_box_batch_equals_the_cell_walk(prec, pose):
         assert lo <= g <= hi
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("periodic", [True, False])
+def test_chain_list_tiny_and_ragged_molecules(prec, periodic):
+    """Molecules of 1 to 33 base pairs (segments and tiles cut anywhere,
+    single-nucleotide strands) in a 20 nm periodic box, just wide enough for 3
+    grid cells per edge, or in an open box: pairs equal to brute force, forces
+    bitwise equal to the cell walk."""
+    cfg = I.ragged_batch([1, 2, 7, 9, 17, 33], seed=4, spread=0.02)
+    box = (20.0, 20.0, 20.0) if periodic else None
+    out, got = [], []
+    for lb in (0, 1):
+        kw = dict(box=box) if periodic else {}
+        p = D.dsdna_default_params(precision=prec, list_build=lb, **kw)
+        ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om)
+        assert ctx.info()["chain_list"] == (lb == 0)
+        got.append({tuple(x) for x in ctx.neighbor_pairs()})
+        out.append(ctx.compute_forces())
+        skin = ctx.params.skin + 0.01
+        ctx.close()
+    po = O.params(box=box) if periodic else O.params()
+    lo = {tuple(x) for x in O.pairs(po, cfg.n_bp, cfg.X, cfg.u, extra=skin - 1e-4)}
+    hi = {tuple(x) for x in O.pairs(po, cfg.n_bp, cfg.X, cfg.u, extra=skin + 1e-4)}
+    for g in got:
+        assert lo <= g <= hi
+    assert len(lo) > 50
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_chain_list_with_every_segment_wide(periodic):
+    """Strand B of a walk moved 4 nm away from strand A: every 16-slot segment
+    is wider than the grid's limit, so every bead enters the segment grid
+    alone and queries it alone.  The list still equals brute force.  (The
+    forces of this configuration stay finite: largest bead force 6e5 kT/nm.)"""
+    cfg = I.random_walk_helix(n_bp=1500, phi=0.02, clearance=1.7, seed=18)
+    X = cfg.X.copy()
+    X[1::2] += np.array([4.0, 0.0, 0.0])      # odd slots: strand B
+    box = cfg.box if periodic else None
+    got = []
+    for lb in (0, 1):
+        kw = dict(box=box) if periodic else {}
+        p = D.dsdna_default_params(list_build=lb, **kw)
+        ctx = D.Context(p, cfg.n_bp, X=X, V=cfg.V, u=cfg.u, Om=cfg.Om)
+        assert ctx.info()["chain_list"] == (lb == 0)
+        got.append({tuple(x) for x in ctx.neighbor_pairs()})
+        skin = ctx.params.skin + 0.01
+        ctx.close()
+    po = O.params(box=box) if periodic else O.params()
+    lo = {tuple(x) for x in O.pairs(po, cfg.n_bp, X, cfg.u, extra=skin - 1e-4)}
+    hi = {tuple(x) for x in O.pairs(po, cfg.n_bp, X, cfg.u, extra=skin + 1e-4)}
+    for g in got:
+        assert lo <= g <= hi
+    assert len(lo) > 800
