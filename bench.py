@@ -461,7 +461,7 @@ def main():
     if not args.no_autotune:
         p, ns = D.dsdna_autotune(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether, trial_steps=30)
         tuned = {"skin": p.skin, "block_threads": p.block_threads, "blocks_per_sm": p.blocks_per_sm,
-                 "trial_ns_per_nt_step": ns}
+                 "list_build": p.list_build, "trial_ns_per_nt_step": ns}
     ctx = D.Context(p, cfg.n_bp, X=cfg.X, V=cfg.V, u=cfg.u, Om=cfg.Om, tether=cfg.tether)
     if cfg.ext_f is not None:
         for m in range(len(cfg.n_bp)):

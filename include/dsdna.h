@@ -337,7 +337,8 @@ void dsdna_destroy(dsdna_ctx* ctx);
  * sys on temporary contexts for every candidate neighbour skin
  * (0.2, 0.25, 0.3, 0.35, 0.4, 0.5, 0.6 nm), CTA size (128, 256, 1024) and persistent CTAs per SM (and, with
  * rebuild_mode 0 and between a quarter and four times
- * DSDNA_FUSED_REBUILD_MAX_NT nucleotides, both rebuild paths), and writes
+ * DSDNA_FUSED_REBUILD_MAX_NT nucleotides, both rebuild paths), then the
+ * fastest of these with the other list_build, and writes
  * to *best the copy of *base with the fastest choice (ns per
  * nucleotide-step in *best_ns, may be NULL).  The candidates change how
  * often the list is rebuilt and how work is spread, never the computed

@@ -1216,6 +1216,24 @@ extern "C" int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys,
   std::vector<int> modes{base->rebuild_mode};
   if (base->rebuild_mode == 0 && n_nt >= DSDNA_FUSED_REBUILD_MAX_NT / 4 && n_nt <= 4 * (int64_t)DSDNA_FUSED_REBUILD_MAX_NT)
     modes = {1, 2};
+  // one timed trial of candidate p (ns per nucleotide-step), keeping the fastest
+  auto trial = [&](const dsdna_params& p) {
+    dsdna_ctx* c = nullptr;
+    if (dsdna_create(&p, sys, alloc, cuda_stream, &c) != DSDNA_OK) { why = g_create_error; return; }
+    float ms = 0.f;
+    bool ok = dsdna_step(c, trial_steps) == DSDNA_OK && dsdna_synchronize(c) == DSDNA_OK;   // warm-up + first build
+    if (ok) {
+      ok = cudaEventRecord(e0, st) == cudaSuccess && dsdna_step(c, trial_steps) == DSDNA_OK &&
+           cudaEventRecord(e1, st) == cudaSuccess && dsdna_synchronize(c) == DSDNA_OK &&
+           cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    }
+    const double t = 1e6 * (double)ms / ((double)trial_steps * (double)c->n);   // ns per nucleotide-step
+    if (!ok) why = c->errmsg.empty() ? std::string("event timing failed") : c->errmsg;
+    dsdna_destroy(c);
+    if (!ok) return;
+    ++tried;
+    if (t < best_t) { best_t = t; winner = p; }
+  };
   for (int rm : modes)
   for (double sk : skins)
     for (int T : blocks)
@@ -1226,22 +1244,15 @@ extern "C" int dsdna_autotune(const dsdna_params* base, const dsdna_system* sys,
         p.skin = sk;
         p.block_threads = T;
         p.blocks_per_sm = ps;
-        dsdna_ctx* c = nullptr;
-        if (dsdna_create(&p, sys, alloc, cuda_stream, &c) != DSDNA_OK) { why = g_create_error; continue; }
-        float ms = 0.f;
-        bool ok = dsdna_step(c, trial_steps) == DSDNA_OK && dsdna_synchronize(c) == DSDNA_OK;   // warm-up + first build
-        if (ok) {
-          ok = cudaEventRecord(e0, st) == cudaSuccess && dsdna_step(c, trial_steps) == DSDNA_OK &&
-               cudaEventRecord(e1, st) == cudaSuccess && dsdna_synchronize(c) == DSDNA_OK &&
-               cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-        }
-        const double t = 1e6 * (double)ms / ((double)trial_steps * (double)c->n);   // ns per nucleotide-step
-        if (!ok) why = c->errmsg.empty() ? std::string("event timing failed") : c->errmsg;
-        dsdna_destroy(c);
-        if (!ok) continue;
-        ++tried;
-        if (t < best_t) { best_t = t; winner = p; }
+        trial(p);
       }
+  // the winner with the other neighbour-list build (the cell walk for the
+  // chain window, or the reverse), in case this system favours it
+  if (tried) {
+    dsdna_params p = winner;
+    p.list_build = winner.list_build == 0 ? 1 : 0;
+    trial(p);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (!tried) return fail(nullptr, DSDNA_ECUDA, "autotune: no candidate ran (last: " + why + ")");
