@@ -79,9 +79,12 @@ def build_workload(name: str, seed: int = 0, n_bp: int = 1_000_000):
 
 # DRAM bytes (read + write) per nucleotide-step of the mixed-precision step
 # kernel from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
-# the bench's multi-step launches on the 1 Mbp confined workload), keyed by a
-# hash of the kernel sources it was taken on: a changed kernel reports no traffic.
-ENGINE_TRAFFIC = {("2798d66a242bfac2", "c3"): 214.5}   # 1 Mbp confined walk, skin 0.3, pair halving
+# the bench's multi-step launches on the 1 Mbp confined workload, pair halving),
+# keyed by a hash of the kernel sources it was taken on and by the skin: a
+# changed kernel, or a skin without a capture, reports no traffic.
+ENGINE_TRAFFIC = {("2798d66a242bfac2", "c3", 0.3): 214.5,
+                  ("2798d66a242bfac2", "c3", 0.35): 215.8,
+                  ("2798d66a242bfac2", "c3", 0.4): 218.0}
 ENGINE_SOURCES = ("engine.cuh", "engine_kernels.cuh", "kern_mixed.cu")   # the step kernel's code
 
 
@@ -94,11 +97,11 @@ def engine_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def engine_traffic_per_nt_step(prec, workload):
+def engine_traffic_per_nt_step(prec, workload, skin):
     from paper_1608_03722_gb300 import dsdna as D
     if prec != D.PREC_MIXED:
         return None
-    return ENGINE_TRAFFIC.get((engine_source_hash(), workload))
+    return ENGINE_TRAFFIC.get((engine_source_hash(), workload, round(float(skin), 2)))
 
 
 def peaks():
@@ -540,11 +543,12 @@ def main():
     launch_s = prof["engine_ms"] * 1e-3 / max(prof["engine_launches"], 1)
     hbm, peak_kind = peaks()
     achieved = per_launch_bytes / launch_s / 1e9
-    traffic = engine_traffic_per_nt_step(prec, args.workload)
+    traffic = engine_traffic_per_nt_step(prec, args.workload, ctx.params.skin)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": None if traffic is None else traffic * cfg.n_nt * steps_per_launch,
             "traffic_capture": None if traffic is None else
-            f"{traffic} B per nucleotide-step from ncu at skin 0.3, scaled by nucleotide-steps per launch",
+            f"{traffic} B per nucleotide-step from ncu at skin {round(float(ctx.params.skin), 2)}, scaled by "
+            f"nucleotide-steps per launch",
             "peak_kind": peak_kind, "bytes_per_nt_step": b_nt, "neighbors_per_bead": nbar,
             "pair_halving": halved, "evaluated_pairs_per_nucleotide": ebar if halved else nbar,
             "algorithmic_bytes_per_launch": per_launch_bytes, "steps_per_launch": steps_per_launch,
