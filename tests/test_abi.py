@@ -84,3 +84,19 @@ def test_create_without_gpu_fails_cleanly():
     rc = L.dsdna_create(C.byref(p), C.byref(sys), None, None, C.byref(h))
     assert rc != 0 and not h.value
     assert L.dsdna_last_error(None)
+
+
+@pytest.mark.parametrize("field,value", [("list_build", 2), ("list_build", -1), ("pair_halving", 2)])
+def test_create_rejects_out_of_range_build_switches(field, value):
+    """Parameter checks come before any device call, so they hold without a
+    GPU: an out-of-range list_build or pair_halving is DSDNA_EINVAL, named in
+    the error text."""
+    L = dsdna.load()
+    p = dsdna.dsdna_default_params()
+    setattr(p, field, value)
+    nb = (C.c_int * 1)(10)
+    sys = dsdna.dsdna_system(1, nb, None, None, None, None, None)
+    h = C.c_void_p()
+    rc = L.dsdna_create(C.byref(p), C.byref(sys), None, None, C.byref(h))
+    assert rc == -1 and not h.value, rc
+    assert field in L.dsdna_last_error(None).decode()
